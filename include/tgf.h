@@ -1,0 +1,179 @@
+/*
+ * tgf.h -- C ABI of libtgf: the twisted Wilson flow of SU(3) link fields on a GB300 (sm_103a).
+ *
+ * The library integrates the Wilson flow dV/dt = Z(V) V, Z = -g0^2 dS_W, of the
+ * twisted Wilson action S_W = 3b sum_n sum_{mu!=nu} Tr[1 - Z*_{mu nu}(n) P_{mu nu}(n)]
+ * (arXiv:2107.03747, Sec. 3.1) with Luscher's third-order Runge-Kutta scheme
+ * (JHEP 08 (2010) 071, cited in Sec. 1), and measures along the flow the clover
+ * energy density E(t) and topological charge Q(t) (Sec. 3.1, eqs. gmunu and qlatt)
+ * and the average twisted plaquette.  Host helpers give the lattice
+ * normalisation N(c, Lt) (eq. latt_norm) and lambda_TGF (eq. lambdat_latt).
+ *
+ * Memory.  The library allocates no device memory.  Every device buffer is
+ * owned by the caller (for example a torch tensor) and passed as a plain
+ * pointer; sizes come from the tgf_*_bytes queries.  Device pointers must be
+ * 256-byte aligned (cudaMalloc and torch allocations are).  Host pointers are
+ * read or written only during the call unless stated otherwise.
+ *
+ * Streams.  `stream` is a cudaStream_t passed as void* (NULL = the legacy
+ * default stream).  Device work is enqueued on it and the call returns without
+ * synchronising unless stated otherwise.
+ *
+ * Errors.  Every call returns a tgf_status; nothing is thrown across the ABI.
+ * On failure tgf_last_error() returns a message (thread-local, valid until the
+ * next failing call on the same thread).  Invalid arguments are rejected before
+ * any device work is enqueued.
+ *
+ * Lattices.  A batch is `ncfg` (1..TGF_MAX_CFG) configurations, each with its
+ * own tgf_lattice: extents L[0..3] (x0 fastest; directions 0, 1 are the short
+ * twisted plane of the l x l x 3l x 3l box, 2, 3 the long periodic ones; every
+ * extent >= 2) and the antisymmetric twist tensor n_{mu nu} mod 3 given by its
+ * six upper entries.  The centre factor Z_{mu nu}(n) = exp(2 pi i n_{mu nu}/3)
+ * sits on the plaquettes whose corner has x_mu = x_nu = 0 (the 0-based reading
+ * of the paper's x_1 = x_2 = 1) and is 1 elsewhere.
+ *
+ * Canonical layout (host and device "canonical" buffers): per configuration
+ * V = L0 L1 L2 L3 sites x 4 directions x 3 x 3 complex doubles, ordered
+ * [x3][x2][x1][x0][mu][row][col][re,im]; configurations follow each other.
+ *
+ * Device storage layout (opaque to callers, described for profiling): per
+ * configuration, per direction, 16-byte-vector planes of Vp = V rounded up to
+ * a multiple of 32 sites -- FP64: nine double2 planes (matrix entries);
+ * FP32: four float4 planes (entries 0-7) and one float2 plane (entry 8);
+ * FP32_R12: three float4 planes holding rows 0 and 1, row 2 being rebuilt on
+ * every load as conj(row0 x row1).  The su(3) accumulator X of the RK3 scheme
+ * holds 8 reals per link in the working precision.
+ */
+#ifndef TGF_H
+#define TGF_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    TGF_OK = 0,
+    TGF_EINVAL = 1,   /* bad argument: extents, twist, sizes, pointers, eps, t_end   */
+    TGF_ECUDA = 3,    /* a CUDA runtime call failed (message in tgf_last_error)      */
+    TGF_EKERNEL = 4,  /* a kernel reported an error (non-finite observable)          */
+    TGF_ESTATE = 6    /* no configuration survived the |Q| < 1/2 cut                  */
+} tgf_status;
+
+typedef enum {
+    TGF_FP64 = 0,     /* links, staples, exponential, X in double                     */
+    TGF_FP32 = 1,     /* links (18 reals), staples, exponential, X in float; sums FP64 */
+    TGF_FP32_R12 = 2  /* as TGF_FP32 with links stored as two rows (12 reals)          */
+} tgf_precision;
+
+#define TGF_MAX_CFG 256
+
+/* Flags of tgf_measure / tgf_flow. */
+#define TGF_CLOVER_TRACELESS 1u   /* subtract tr(G)/3 from the clover G (eq. gmunu has no projection) */
+#define TGF_NO_GRAPH 2u           /* tgf_flow: launch kernels directly instead of one CUDA graph      */
+
+typedef struct {
+    int L[4];      /* extents, x0 fastest                                          */
+    int twist[6];  /* n_01, n_02, n_03, n_12, n_13, n_23 (any integers, taken mod 3) */
+} tgf_lattice;
+
+/* One measurement of one configuration (Sec. 3.1).
+ *   t  flow time
+ *   E  (1/V) sum_n 1/2 Tr[G_{mu nu} G_{mu nu}]                       clover energy density
+ *   Q  1/(16 pi^2) sum_n Tr[G_{mu nu} Gt_{mu nu}]                    clover topological charge
+ *   P  (1/(6V)) sum_n sum_{mu<nu} 1/3 Re Tr[Z*_{mu nu} P_{mu nu}]   average twisted plaquette
+ *   S  sum_n sum_{mu<nu} Re Tr[1 - Z* P] = g0^2 S_W / 2              reduced twisted action   */
+typedef struct {
+    double t, E, Q, P, S;
+} tgf_obs;
+
+/* ---- sizes ---------------------------------------------------------------------------- */
+
+/* Bytes of device link storage for the batch in precision `prec` (see layout above). */
+tgf_status tgf_links_bytes(int prec, const tgf_lattice *lat, int ncfg, size_t *bytes);
+/* Bytes of the RK3 accumulator X (8 reals per link in the working precision). */
+tgf_status tgf_accum_bytes(int prec, const tgf_lattice *lat, int ncfg, size_t *bytes);
+/* Bytes of the scratch buffer that tgf_measure and tgf_flow use for per-block partial sums. */
+tgf_status tgf_scratch_bytes(const tgf_lattice *lat, int ncfg, size_t *bytes);
+/* Bytes of one configuration's canonical FP64 field: V * 4 * 9 * 16. */
+tgf_status tgf_canonical_bytes(const tgf_lattice *lat, size_t *bytes);
+
+/* ---- layout conversion (Sec. 3.1 links U_mu(n)) --------------------------------------- */
+
+/* Canonical FP64 device buffer (all configurations) -> device storage `links`. FP32 forms
+ * round to nearest; FP32_R12 keeps rows 0 and 1. */
+tgf_status tgf_pack(int prec, const tgf_lattice *lat, int ncfg, const double *canon_dev,
+                    void *links, void *stream);
+/* Device storage -> canonical FP64 device buffer (FP32_R12 rebuilds row 2). */
+tgf_status tgf_unpack(int prec, const tgf_lattice *lat, int ncfg, const void *links,
+                      double *canon_dev, void *stream);
+/* Host canonical buffer -> device storage, one configuration at a time through the caller's
+ * device staging buffer of at least max-over-configurations tgf_canonical_bytes.  The host
+ * buffer should be pinned for the copies to be asynchronous; it must stay valid until the
+ * stream reaches this point. */
+tgf_status tgf_upload(int prec, const tgf_lattice *lat, int ncfg, const double *canon_host,
+                      double *staging_dev, size_t staging_bytes, void *links, void *stream);
+/* Device storage -> host canonical buffer through the staging buffer; synchronises `stream`. */
+tgf_status tgf_download(int prec, const tgf_lattice *lat, int ncfg, const void *links,
+                        double *staging_dev, size_t staging_bytes, double *canon_host, void *stream);
+
+/* ---- the hot path ----------------------------------------------------------------------- */
+
+/* One stage s = 1, 2, 3 of the low-storage RK3 step of size eps for every link of the batch:
+ * Z = -P_ta(U_mu Sigma_mu) from the twisted staples of `w_in`; then
+ *   s=1: X = eps Z/4;   s=2: X = 8/9 eps Z - 17/9 X;   s=3: X = 3/4 eps Z - X;
+ * and w_out = exp(X) w_in (exact SU(3) exponential).  The three stages equal Luscher's
+ * W1 = e^{Z0/4} W0, W2 = e^{8/9 Z1 - 17/36 Z0} W1, W3 = e^{3/4 Z2 - 8/9 Z1 + 17/36 Z0} W2.
+ * w_in and w_out must not overlap.  reunit != 0 (stage 3, FP32 forms) re-projects w_out onto
+ * SU(3) by Gram-Schmidt in FP64 before storing. */
+tgf_status tgf_stage(int prec, const tgf_lattice *lat, int ncfg, const void *w_in, void *w_out,
+                     void *accum, int stage, double eps, int reunit, void *stream);
+
+/* Measure every configuration of `links` at flow time t: obs_dev[c * obs_stride + rec] receives
+ * {t, E, Q, P, S} of configuration c.  `scratch` holds the per-block partial sums (size from
+ * tgf_scratch_bytes).  Sums are taken in FP64 in a fixed order (bitwise reproducible). */
+tgf_status tgf_measure(int prec, const tgf_lattice *lat, int ncfg, const void *links,
+                       double *scratch, size_t scratch_bytes, tgf_obs *obs_dev, size_t obs_stride,
+                       int rec, double t, unsigned flags, void *stream);
+
+/* Flow every configuration c from t = 0 to t_end[c] (host array) in RK3 steps of eps: n_c =
+ * floor(t_end[c]/eps) full steps, then one step of t_end[c] - n_c eps if that is > 1e-12 eps.
+ * Observables are recorded into obs_dev[c * obs_cap + r] before every measure_every-th step
+ * and once at t_end[c]; n_records[c] (host) receives the count.  `w` holds the start field and
+ * receives the flowed one; `w_tmp` (same size) is the second ping-pong buffer; `accum` is X.
+ * FP32 forms re-project onto SU(3) every `reunit_every` steps (0 = never).  By default the
+ * whole flow is captured once into a CUDA graph and launched on `stream` (TGF_NO_GRAPH
+ * launches the kernels directly).  Returns without synchronising. */
+tgf_status tgf_flow(int prec, const tgf_lattice *lat, int ncfg, void *w, void *w_tmp, void *accum,
+                    double *scratch, size_t scratch_bytes, double eps, const double *t_end,
+                    int measure_every, int reunit_every, unsigned flags, tgf_obs *obs_dev,
+                    size_t obs_cap, int *n_records, void *stream);
+
+/* Number of records tgf_flow writes for one configuration (host arithmetic only). */
+tgf_status tgf_flow_records(double eps, double t_end, int measure_every, int *n_records);
+
+/* ---- coupling (host only) ----------------------------------------------------------------- */
+
+/* N(c, Lt) of eq. (latt_norm) for SU(N): the inverse of
+ * (c^4/128) sum_{mu!=nu} sum'_q exp(-c^2 Lt^2 qhat^2/4) sin^2(q_nu) cos^2(q_mu/2)/qhat^2
+ * over q_mu = 2 pi n_mu/Lt, n_mu = 0..Lt-1, dropping n_0 = n_1 = 0 (mod N).  O(Lt^4) work. */
+tgf_status tgf_norm(double c, int Ltilde, int N, double *norm_out);
+
+/* lambda_TGF = N(c, Lt) t^2 sum_i E_i d_i / (3 sum_i d_i), d_i = [|Q_i| < 1/2] (eq. lambdat_latt).
+ * Returns TGF_ESTATE (and n_kept = 0) when no configuration passes the cut. */
+tgf_status tgf_lambda(double c, int Ltilde, double t, const double *E, const double *Q, int ncfg,
+                      double *lambda_out, int *n_kept);
+
+/* ---- diagnostics ---------------------------------------------------------------------------- */
+
+const char *tgf_last_error(void);
+const char *tgf_status_string(int status);
+/* Library version, "major.minor.patch". */
+const char *tgf_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TGF_H */

@@ -1,0 +1,301 @@
+"""Thin ctypes binding of libtgf (include/tgf.h): the same entry points, argument marshalling only.
+
+Device buffers are torch tensors (the caller owns them); streams are torch streams.  Every
+call raises ``TgfError`` with the library's message when the status is not TGF_OK.  The
+library must be built first (``paper_2107_03747_gb300.build.build()``); importing this
+module without it raises, there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "libtgf.so")
+
+TGF_OK, TGF_EINVAL, TGF_ECUDA, TGF_EKERNEL, TGF_ESTATE = 0, 1, 3, 4, 6
+TGF_FP64, TGF_FP32, TGF_FP32_R12 = 0, 1, 2
+TGF_CLOVER_TRACELESS = 1
+TGF_NO_GRAPH = 2
+TGF_MAX_CFG = 256
+PRECISIONS = {"fp64": TGF_FP64, "fp32": TGF_FP32, "fp32_r12": TGF_FP32_R12}
+
+
+class TgfError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"tgf status {status}: {msg}")
+        self.status = status
+
+
+class tgf_lattice(C.Structure):
+    _fields_ = [("L", C.c_int * 4), ("twist", C.c_int * 6)]
+
+
+class tgf_obs(C.Structure):
+    _fields_ = [("t", C.c_double), ("E", C.c_double), ("Q", C.c_double), ("P", C.c_double), ("S", C.c_double)]
+
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is missing: build it with paper_2107_03747_gb300.build.build()")
+_lib = C.CDLL(LIB_PATH)
+
+_P = C.c_void_p
+_SZ = C.c_size_t
+_LATP = C.POINTER(tgf_lattice)
+_SIGS = {
+    "tgf_links_bytes": [C.c_int, _LATP, C.c_int, C.POINTER(_SZ)],
+    "tgf_accum_bytes": [C.c_int, _LATP, C.c_int, C.POINTER(_SZ)],
+    "tgf_scratch_bytes": [_LATP, C.c_int, C.POINTER(_SZ)],
+    "tgf_canonical_bytes": [_LATP, C.POINTER(_SZ)],
+    "tgf_pack": [C.c_int, _LATP, C.c_int, _P, _P, _P],
+    "tgf_unpack": [C.c_int, _LATP, C.c_int, _P, _P, _P],
+    "tgf_upload": [C.c_int, _LATP, C.c_int, _P, _P, _SZ, _P, _P],
+    "tgf_download": [C.c_int, _LATP, C.c_int, _P, _P, _SZ, _P, _P],
+    "tgf_stage": [C.c_int, _LATP, C.c_int, _P, _P, _P, C.c_int, C.c_double, C.c_int, _P],
+    "tgf_measure": [C.c_int, _LATP, C.c_int, _P, _P, _SZ, _P, _SZ, C.c_int, C.c_double, C.c_uint, _P],
+    "tgf_flow": [C.c_int, _LATP, C.c_int, _P, _P, _P, _P, _SZ, C.c_double, C.POINTER(C.c_double), C.c_int,
+                 C.c_int, C.c_uint, _P, _SZ, C.POINTER(C.c_int), _P],
+    "tgf_flow_records": [C.c_double, C.c_double, C.c_int, C.POINTER(C.c_int)],
+    "tgf_norm": [C.c_double, C.c_int, C.c_int, C.POINTER(C.c_double)],
+    "tgf_lambda": [C.c_double, C.c_int, C.c_double, C.POINTER(C.c_double), C.POINTER(C.c_double), C.c_int,
+                   C.POINTER(C.c_double), C.POINTER(C.c_int)],
+}
+for _name, _args in _SIGS.items():
+    _f = getattr(_lib, _name)
+    _f.argtypes = _args
+    _f.restype = C.c_int
+_lib.tgf_last_error.restype = C.c_char_p
+_lib.tgf_last_error.argtypes = []
+_lib.tgf_status_string.restype = C.c_char_p
+_lib.tgf_status_string.argtypes = [C.c_int]
+_lib.tgf_version.restype = C.c_char_p
+_lib.tgf_version.argtypes = []
+
+EXPORTED = sorted(list(_SIGS) + ["tgf_last_error", "tgf_status_string", "tgf_version"])
+
+
+def _check(status: int):
+    if status != TGF_OK:
+        raise TgfError(status, _lib.tgf_last_error().decode())
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    return t.data_ptr()
+
+
+def _stream(stream):
+    import torch
+
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream
+
+
+def lattices(Ls, twists=None):
+    """ctypes array of tgf_lattice from extents (L0, L1, L2, L3) and twist 6-tuples (default n_01 = 1)."""
+    n = len(Ls)
+    arr = (tgf_lattice * n)()
+    for i, L in enumerate(Ls):
+        arr[i].L[:] = [int(x) for x in L]
+        tw = (1, 0, 0, 0, 0, 0) if twists is None else twists[i]
+        arr[i].twist[:] = [int(x) for x in tw]
+    return arr
+
+
+def twist6(n):
+    """Six upper entries (01, 02, 03, 12, 13, 23) of a 4x4 antisymmetric twist tensor."""
+    return tuple(int(n[a][b]) for a, b in ((0, 1), (0, 2), (0, 3), (1, 2), (1, 3), (2, 3)))
+
+
+def version() -> str:
+    return _lib.tgf_version().decode()
+
+
+def status_string(s: int) -> str:
+    return _lib.tgf_status_string(s).decode()
+
+
+def tgf_links_bytes(prec, lat) -> int:
+    out = _SZ()
+    _check(_lib.tgf_links_bytes(prec, lat, len(lat), C.byref(out)))
+    return out.value
+
+
+def tgf_accum_bytes(prec, lat) -> int:
+    out = _SZ()
+    _check(_lib.tgf_accum_bytes(prec, lat, len(lat), C.byref(out)))
+    return out.value
+
+
+def tgf_scratch_bytes(lat) -> int:
+    out = _SZ()
+    _check(_lib.tgf_scratch_bytes(lat, len(lat), C.byref(out)))
+    return out.value
+
+
+def tgf_canonical_bytes(lat1) -> int:
+    out = _SZ()
+    _check(_lib.tgf_canonical_bytes(lat1, C.byref(out)))
+    return out.value
+
+
+def tgf_pack(prec, lat, canon_dev, links, stream=None):
+    _check(_lib.tgf_pack(prec, lat, len(lat), _ptr(canon_dev), _ptr(links), _stream(stream)))
+
+
+def tgf_unpack(prec, lat, links, canon_dev, stream=None):
+    _check(_lib.tgf_unpack(prec, lat, len(lat), _ptr(links), _ptr(canon_dev), _stream(stream)))
+
+
+def tgf_upload(prec, lat, canon_host, staging, links, stream=None):
+    """canon_host: a (pinned) CPU tensor or numpy complex128 array in canonical layout."""
+    p = canon_host.ctypes.data if isinstance(canon_host, np.ndarray) else canon_host.data_ptr()
+    _check(_lib.tgf_upload(prec, lat, len(lat), p, _ptr(staging), staging.numel() * staging.element_size(),
+                           _ptr(links), _stream(stream)))
+
+
+def tgf_download(prec, lat, links, staging, canon_host, stream=None):
+    p = canon_host.ctypes.data if isinstance(canon_host, np.ndarray) else canon_host.data_ptr()
+    _check(_lib.tgf_download(prec, lat, len(lat), _ptr(links), _ptr(staging),
+                             staging.numel() * staging.element_size(), p, _stream(stream)))
+
+
+def tgf_stage(prec, lat, w_in, w_out, accum, stage, eps, reunit=0, stream=None):
+    _check(_lib.tgf_stage(prec, lat, len(lat), _ptr(w_in), _ptr(w_out), _ptr(accum), stage, eps, reunit,
+                          _stream(stream)))
+
+
+def tgf_measure(prec, lat, links, scratch, obs_dev, obs_stride, rec, t, flags=0, stream=None):
+    _check(_lib.tgf_measure(prec, lat, len(lat), _ptr(links), _ptr(scratch),
+                            scratch.numel() * scratch.element_size(), _ptr(obs_dev), obs_stride, rec, t, flags,
+                            _stream(stream)))
+
+
+def tgf_flow_records(eps, t_end, measure_every=1) -> int:
+    out = C.c_int()
+    _check(_lib.tgf_flow_records(eps, t_end, measure_every, C.byref(out)))
+    return out.value
+
+
+def tgf_flow(prec, lat, w, w_tmp, accum, scratch, eps, t_end, obs_dev, obs_cap, measure_every=1,
+             reunit_every=0, flags=0, stream=None):
+    """Returns the number of records written per configuration (list)."""
+    n = len(lat)
+    te = (C.c_double * n)(*[float(x) for x in t_end])
+    nrec = (C.c_int * n)()
+    _check(_lib.tgf_flow(prec, lat, n, _ptr(w), _ptr(w_tmp), _ptr(accum), _ptr(scratch),
+                         scratch.numel() * scratch.element_size(), eps, te, measure_every, reunit_every, flags,
+                         _ptr(obs_dev), obs_cap, nrec, _stream(stream)))
+    return list(nrec)
+
+
+def tgf_norm(c, Lt, N=3) -> float:
+    out = C.c_double()
+    _check(_lib.tgf_norm(c, Lt, N, C.byref(out)))
+    return out.value
+
+
+def tgf_lambda(c, Lt, t, E, Q):
+    """(lambda, n_kept); lambda is None when no configuration has |Q| < 1/2."""
+    n = len(E)
+    Ea = (C.c_double * n)(*[float(x) for x in E])
+    Qa = (C.c_double * n)(*[float(x) for x in Q])
+    lam = C.c_double()
+    kept = C.c_int()
+    s = _lib.tgf_lambda(c, Lt, t, Ea, Qa, n, C.byref(lam), C.byref(kept))
+    if s == TGF_ESTATE:
+        return None, 0
+    _check(s)
+    return lam.value, kept.value
+
+
+# ---------------------------------------------------------------------------------------------
+# convenience: a batch of configurations with its device buffers (torch tensors)
+# ---------------------------------------------------------------------------------------------
+
+class FlowBatch:
+    """Device buffers for flowing a batch of configurations in one precision.
+
+    ``links`` holds the current field; ``links_tmp`` and ``accum`` are the RK3 work buffers;
+    ``scratch`` the measurement partials.  All are torch uint8 tensors on ``device``.
+    """
+
+    def __init__(self, Ls, prec="fp64", twists=None, device="cuda"):
+        import torch
+
+        self.prec = PRECISIONS[prec] if isinstance(prec, str) else int(prec)
+        self.lat = lattices(Ls, twists)
+        self.Ls = [tuple(int(x) for x in L) for L in Ls]
+        self.device = torch.device(device)
+        nb = tgf_links_bytes(self.prec, self.lat)
+        self.links = torch.empty(nb, dtype=torch.uint8, device=self.device)
+        self.links_tmp = torch.empty(nb, dtype=torch.uint8, device=self.device)
+        self.accum = torch.empty(tgf_accum_bytes(self.prec, self.lat), dtype=torch.uint8, device=self.device)
+        self.scratch = torch.empty(tgf_scratch_bytes(self.lat), dtype=torch.uint8, device=self.device)
+
+    @property
+    def ncfg(self):
+        return len(self.Ls)
+
+    def canonical_numel(self):
+        return sum(L[0] * L[1] * L[2] * L[3] * 72 for L in self.Ls)
+
+    def set_links(self, fields, stream=None):
+        """fields: list of complex128 numpy arrays in canonical layout, one per configuration."""
+        import torch
+
+        flat = np.concatenate([np.ascontiguousarray(f).view(np.float64).reshape(-1) for f in fields])
+        canon = torch.from_numpy(flat).to(self.device)
+        tgf_pack(self.prec, self.lat, canon, self.links, stream)
+        return canon
+
+    def set_links_device(self, canon_dev, stream=None):
+        tgf_pack(self.prec, self.lat, canon_dev, self.links, stream)
+
+    def get_links(self, stream=None):
+        """Current fields as complex128 numpy arrays in canonical layout."""
+        import torch
+
+        canon = torch.empty(self.canonical_numel(), dtype=torch.float64, device=self.device)
+        tgf_unpack(self.prec, self.lat, self.links, canon, stream)
+        flat = canon.cpu().numpy()
+        out, off = [], 0
+        for L in self.Ls:
+            n = L[0] * L[1] * L[2] * L[3] * 72
+            out.append(flat[off:off + n].view(np.complex128).reshape(L[3], L[2], L[1], L[0], 4, 3, 3))
+            off += n
+        return out
+
+    def measure(self, t=0.0, flags=0, stream=None):
+        """{t, E, Q, P, S} per configuration as an (ncfg, 5) numpy array."""
+        import torch
+
+        obs = torch.zeros(self.ncfg * 5, dtype=torch.float64, device=self.device)
+        tgf_measure(self.prec, self.lat, self.links, self.scratch, obs, 1, 0, t, flags, stream)
+        return obs.cpu().numpy().reshape(self.ncfg, 5)
+
+    def stage(self, stage, eps, reunit=0, stream=None):
+        """One RK3 stage from ``links`` into ``links_tmp``; then the two are swapped."""
+        tgf_stage(self.prec, self.lat, self.links, self.links_tmp, self.accum, stage, eps, reunit, stream)
+        self.links, self.links_tmp = self.links_tmp, self.links
+
+    def flow(self, eps, t_end, measure_every=1, reunit_every=0, flags=0, stream=None, obs=None):
+        """Flow every configuration to t_end (scalar or per-configuration list).
+
+        Returns (obs tensor of shape (ncfg, cap, 5) on the device, records per configuration).
+        """
+        import torch
+
+        te = [float(t_end)] * self.ncfg if np.isscalar(t_end) else [float(x) for x in t_end]
+        cap = max(tgf_flow_records(eps, t, measure_every) for t in te)
+        if obs is None or obs.numel() < self.ncfg * cap * 5:
+            obs = torch.zeros(self.ncfg * cap * 5, dtype=torch.float64, device=self.device)
+        nrec = tgf_flow(self.prec, self.lat, self.links, self.links_tmp, self.accum, self.scratch, eps, te, obs,
+                        cap, measure_every, reunit_every, flags, stream)
+        return obs[: self.ncfg * cap * 5].view(self.ncfg, cap, 5), nrec

@@ -1,0 +1,504 @@
+// api.cu -- the C ABI of libtgf (declared in include/tgf.h): argument checks, batch
+// descriptors, and the flow driver that sequences the stage / measure / reduce kernels
+// and captures a whole flow into one CUDA graph.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <list>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/tgf.h"
+#include "lattice.cuh"
+
+using namespace tgf;
+
+namespace {
+
+thread_local std::string g_err;
+
+tgf_status fail(tgf_status st, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return st;
+}
+
+#define TGF_CUDA(call)                                                                          \
+    do {                                                                                        \
+        cudaError_t e_ = (call);                                                                \
+        if (e_ != cudaSuccess) return fail(TGF_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+int reals_of(int prec) { return prec == TGF_FP32_R12 ? 12 : 18; }
+size_t real_size(int prec) { return prec == TGF_FP64 ? 8 : 4; }
+
+int64_t padded(int64_t V) { return (V + kSiteAlign - 1) / kSiteAlign * kSiteAlign; }
+
+int64_t sites(const tgf_lattice& l) { return (int64_t)l.L[0] * l.L[1] * l.L[2] * l.L[3]; }
+
+tgf_status check_prec(int prec) {
+    if (prec != TGF_FP64 && prec != TGF_FP32 && prec != TGF_FP32_R12)
+        return fail(TGF_EINVAL, "unknown precision %d", prec);
+    return TGF_OK;
+}
+
+tgf_status check_lat(const tgf_lattice* lat, int ncfg) {
+    if (!lat) return fail(TGF_EINVAL, "lattice array is NULL");
+    if (ncfg < 1 || ncfg > TGF_MAX_CFG) return fail(TGF_EINVAL, "ncfg = %d outside 1..%d", ncfg, TGF_MAX_CFG);
+    for (int c = 0; c < ncfg; ++c) {
+        for (int mu = 0; mu < 4; ++mu)
+            if (lat[c].L[mu] < 2 || lat[c].L[mu] > 4096)
+                return fail(TGF_EINVAL, "configuration %d: extent L[%d] = %d outside 2..4096", c, mu, lat[c].L[mu]);
+        if (sites(lat[c]) > (int64_t(1) << 28))
+            return fail(TGF_EINVAL, "configuration %d: %lld sites exceed 2^28", c, (long long)sites(lat[c]));
+    }
+    return TGF_OK;
+}
+
+// n_{mu nu} mod 3 table from the six upper entries
+void twist_table(const tgf_lattice& l, int8_t tw[16]) {
+    const int pairs[6][2] = {{0, 1}, {0, 2}, {0, 3}, {1, 2}, {1, 3}, {2, 3}};
+    std::memset(tw, 0, 16);
+    for (int i = 0; i < 6; ++i) {
+        int k = ((l.twist[i] % 3) + 3) % 3;
+        int mu = pairs[i][0], nu = pairs[i][1];
+        tw[mu * 4 + nu] = (int8_t)k;
+        tw[nu * 4 + mu] = (int8_t)((3 - k) % 3);
+    }
+}
+
+struct Layout {
+    std::vector<int64_t> w_off, x_off, c_off;  // reals / reals / canonical doubles
+    std::vector<int64_t> meas_blk0;            // first measure block of each config in a full launch
+    int64_t w_total = 0, x_total = 0, meas_blocks = 0;
+};
+
+Layout layout(int prec, const tgf_lattice* lat, int ncfg) {
+    Layout L;
+    int64_t w = 0, x = 0, cc = 0, mb = 0;
+    for (int c = 0; c < ncfg; ++c) {
+        int64_t V = sites(lat[c]), Vp = padded(V);
+        L.w_off.push_back(w);
+        L.x_off.push_back(x);
+        L.c_off.push_back(cc);
+        L.meas_blk0.push_back(mb);
+        w += 4 * (int64_t)reals_of(prec) * Vp;
+        x += 4 * 8 * Vp;
+        cc += V * 72;
+        mb += (V + kMeasureSites - 1) / kMeasureSites;
+    }
+    L.w_total = w;
+    L.x_total = x;
+    L.meas_blocks = mb;
+    return L;
+}
+
+// Descriptor of a launch over the configurations `which`, `spb` sites per block.
+Batch make_batch(const tgf_lattice* lat, const Layout& Ly, const std::vector<int>& which, int spb) {
+    Batch B;
+    B.ncfg = (int)which.size();
+    int blk = 0;
+    for (int i = 0; i < B.ncfg; ++i) {
+        const int c = which[i];
+        CfgDesc& d = B.c[i];
+        for (int mu = 0; mu < 4; ++mu) d.L[mu] = lat[c].L[mu];
+        d.V = (int)sites(lat[c]);
+        d.Vp = (int)padded(d.V);
+        d.blk0 = blk;
+        d.rec = 0;
+        d.w_off = Ly.w_off[c];
+        d.x_off = Ly.x_off[c];
+        d.o_off = 0;
+        d.h = 0.0;
+        twist_table(lat[c], d.tw);
+        blk += (d.V + spb - 1) / spb;
+    }
+    B.nblk = blk;
+    return B;
+}
+
+std::vector<int> all_cfgs(int ncfg) {
+    std::vector<int> v(ncfg);
+    for (int i = 0; i < ncfg; ++i) v[i] = i;
+    return v;
+}
+
+tgf_status last_launch(const char* what) {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(TGF_ECUDA, "%s launch: %s", what, cudaGetErrorString(e));
+    return TGF_OK;
+}
+
+// measure + reduce over `which`, record r_c at time t_c
+tgf_status enqueue_measure(int prec, unsigned flags, const tgf_lattice* lat, const Layout& Ly,
+                           const std::vector<int>& which, const std::vector<int>& rec, const std::vector<double>& t,
+                           size_t obs_stride, const void* w, double* scratch, tgf_obs* obs, cudaStream_t st) {
+    Batch B = make_batch(lat, Ly, which, kMeasureSites);
+    for (int i = 0; i < B.ncfg; ++i) {
+        B.c[i].rec = rec[i];
+        B.c[i].h = t[i];
+        B.c[i].o_off = (int64_t)which[i] * (int64_t)obs_stride + rec[i];
+    }
+    launch_measure(prec, flags, B, w, scratch, st);
+    tgf_status s = last_launch("measure");
+    if (s) return s;
+    launch_reduce(B, scratch, reinterpret_cast<double*>(obs), st);
+    return last_launch("reduce");
+}
+
+tgf_status check_ptr(const void* p, const char* name) {
+    if (!p) return fail(TGF_EINVAL, "%s is NULL", name);
+    if (reinterpret_cast<uintptr_t>(p) % 256 != 0) return fail(TGF_EINVAL, "%s is not 256-byte aligned", name);
+    return TGF_OK;
+}
+
+void flow_counts(double eps, double t_end, int64_t& n, double& rest) {
+    n = (int64_t)std::floor(t_end / eps + 1e-9);
+    rest = t_end - (double)n * eps;
+    if (rest <= 1e-12 * eps) rest = 0.0;
+}
+
+int64_t records_of(int64_t n, double rest, int measure_every) {
+    int64_t total = n + (rest > 0 ? 1 : 0);
+    return (total + measure_every - 1) / measure_every + 1;
+}
+
+// ---- graph cache ----------------------------------------------------------------------------
+
+struct GraphEntry {
+    std::string key;
+    int device;
+    cudaGraphExec_t exec;
+};
+std::mutex g_graph_mu;
+std::list<GraphEntry> g_graphs;  // most recent first
+constexpr size_t kGraphCache = 8;
+cudaStream_t g_capture[64] = {};
+
+}  // namespace
+
+extern "C" {
+
+const char* tgf_last_error(void) { return g_err.c_str(); }
+
+const char* tgf_status_string(int status) {
+    switch (status) {
+        case TGF_OK: return "ok";
+        case TGF_EINVAL: return "invalid argument";
+        case TGF_ECUDA: return "CUDA error";
+        case TGF_EKERNEL: return "kernel error";
+        case TGF_ESTATE: return "no configuration kept";
+        default: return "unknown status";
+    }
+}
+
+const char* tgf_version(void) { return "1.0.0"; }
+
+tgf_status tgf_links_bytes(int prec, const tgf_lattice* lat, int ncfg, size_t* bytes) {
+    tgf_status s;
+    if ((s = check_prec(prec)) || (s = check_lat(lat, ncfg))) return s;
+    if (!bytes) return fail(TGF_EINVAL, "bytes is NULL");
+    *bytes = (size_t)layout(prec, lat, ncfg).w_total * real_size(prec);
+    return TGF_OK;
+}
+
+tgf_status tgf_accum_bytes(int prec, const tgf_lattice* lat, int ncfg, size_t* bytes) {
+    tgf_status s;
+    if ((s = check_prec(prec)) || (s = check_lat(lat, ncfg))) return s;
+    if (!bytes) return fail(TGF_EINVAL, "bytes is NULL");
+    *bytes = (size_t)layout(prec, lat, ncfg).x_total * real_size(prec);
+    return TGF_OK;
+}
+
+tgf_status tgf_scratch_bytes(const tgf_lattice* lat, int ncfg, size_t* bytes) {
+    tgf_status s;
+    if ((s = check_lat(lat, ncfg))) return s;
+    if (!bytes) return fail(TGF_EINVAL, "bytes is NULL");
+    *bytes = (size_t)layout(TGF_FP64, lat, ncfg).meas_blocks * kPartials * sizeof(double);
+    return TGF_OK;
+}
+
+tgf_status tgf_canonical_bytes(const tgf_lattice* lat, size_t* bytes) {
+    tgf_status s;
+    if ((s = check_lat(lat, 1))) return s;
+    if (!bytes) return fail(TGF_EINVAL, "bytes is NULL");
+    *bytes = (size_t)sites(*lat) * 72 * sizeof(double);
+    return TGF_OK;
+}
+
+tgf_status tgf_pack(int prec, const tgf_lattice* lat, int ncfg, const double* canon_dev, void* links, void* stream) {
+    tgf_status s;
+    if ((s = check_prec(prec)) || (s = check_lat(lat, ncfg)) || (s = check_ptr(canon_dev, "canon_dev")) ||
+        (s = check_ptr(links, "links")))
+        return s;
+    Layout Ly = layout(prec, lat, ncfg);
+    Batch B = make_batch(lat, Ly, all_cfgs(ncfg), 32);
+    for (int i = 0; i < ncfg; ++i) B.c[i].x_off = Ly.c_off[i];
+    launch_pack(prec, B, canon_dev, links, (cudaStream_t)stream);
+    return last_launch("pack");
+}
+
+tgf_status tgf_unpack(int prec, const tgf_lattice* lat, int ncfg, const void* links, double* canon_dev, void* stream) {
+    tgf_status s;
+    if ((s = check_prec(prec)) || (s = check_lat(lat, ncfg)) || (s = check_ptr(canon_dev, "canon_dev")) ||
+        (s = check_ptr(links, "links")))
+        return s;
+    Layout Ly = layout(prec, lat, ncfg);
+    Batch B = make_batch(lat, Ly, all_cfgs(ncfg), 32);
+    for (int i = 0; i < ncfg; ++i) B.c[i].x_off = Ly.c_off[i];
+    launch_unpack(prec, B, links, canon_dev, (cudaStream_t)stream);
+    return last_launch("unpack");
+}
+
+static tgf_status check_staging(const tgf_lattice* lat, int ncfg, const double* staging, size_t staging_bytes) {
+    tgf_status s;
+    if ((s = check_ptr(staging, "staging_dev"))) return s;
+    for (int c = 0; c < ncfg; ++c)
+        if ((size_t)sites(lat[c]) * 72 * sizeof(double) > staging_bytes)
+            return fail(TGF_EINVAL, "staging buffer of %zu bytes too small for configuration %d", staging_bytes, c);
+    return TGF_OK;
+}
+
+tgf_status tgf_upload(int prec, const tgf_lattice* lat, int ncfg, const double* canon_host, double* staging_dev,
+                      size_t staging_bytes, void* links, void* stream) {
+    tgf_status s;
+    if ((s = check_prec(prec)) || (s = check_lat(lat, ncfg)) || (s = check_ptr(links, "links")) ||
+        (s = check_staging(lat, ncfg, staging_dev, staging_bytes)))
+        return s;
+    if (!canon_host) return fail(TGF_EINVAL, "canon_host is NULL");
+    cudaStream_t st = (cudaStream_t)stream;
+    Layout Ly = layout(prec, lat, ncfg);
+    for (int c = 0; c < ncfg; ++c) {
+        TGF_CUDA(cudaMemcpyAsync(staging_dev, canon_host + Ly.c_off[c], (size_t)sites(lat[c]) * 72 * sizeof(double),
+                                 cudaMemcpyHostToDevice, st));
+        Batch B = make_batch(lat, Ly, std::vector<int>{c}, 32);
+        B.c[0].x_off = 0;
+        launch_pack(prec, B, staging_dev, links, st);
+        if ((s = last_launch("pack"))) return s;
+    }
+    return TGF_OK;
+}
+
+tgf_status tgf_download(int prec, const tgf_lattice* lat, int ncfg, const void* links, double* staging_dev,
+                        size_t staging_bytes, double* canon_host, void* stream) {
+    tgf_status s;
+    if ((s = check_prec(prec)) || (s = check_lat(lat, ncfg)) || (s = check_ptr(links, "links")) ||
+        (s = check_staging(lat, ncfg, staging_dev, staging_bytes)))
+        return s;
+    if (!canon_host) return fail(TGF_EINVAL, "canon_host is NULL");
+    cudaStream_t st = (cudaStream_t)stream;
+    Layout Ly = layout(prec, lat, ncfg);
+    for (int c = 0; c < ncfg; ++c) {
+        Batch B = make_batch(lat, Ly, std::vector<int>{c}, 32);
+        B.c[0].x_off = 0;
+        launch_unpack(prec, B, links, staging_dev, st);
+        if ((s = last_launch("unpack"))) return s;
+        TGF_CUDA(cudaMemcpyAsync(canon_host + Ly.c_off[c], staging_dev, (size_t)sites(lat[c]) * 72 * sizeof(double),
+                                 cudaMemcpyDeviceToHost, st));
+        TGF_CUDA(cudaStreamSynchronize(st));
+    }
+    return TGF_OK;
+}
+
+tgf_status tgf_stage(int prec, const tgf_lattice* lat, int ncfg, const void* w_in, void* w_out, void* accum, int stage,
+                     double eps, int reunit, void* stream) {
+    tgf_status s;
+    if ((s = check_prec(prec)) || (s = check_lat(lat, ncfg)) || (s = check_ptr(w_in, "w_in")) ||
+        (s = check_ptr(w_out, "w_out")) || (s = check_ptr(accum, "accum")))
+        return s;
+    if (stage < 1 || stage > 3) return fail(TGF_EINVAL, "stage %d outside 1..3", stage);
+    if (!(std::isfinite(eps)) || eps == 0.0) return fail(TGF_EINVAL, "eps = %g must be finite and non-zero", eps);
+    if (w_in == w_out) return fail(TGF_EINVAL, "w_in and w_out must be distinct buffers");
+    Layout Ly = layout(prec, lat, ncfg);
+    Batch B = make_batch(lat, Ly, all_cfgs(ncfg), 32);
+    for (int i = 0; i < ncfg; ++i) B.c[i].h = eps;
+    launch_stage(prec, stage, reunit, B, w_in, w_out, accum, 32, (cudaStream_t)stream);
+    return last_launch("stage");
+}
+
+tgf_status tgf_measure(int prec, const tgf_lattice* lat, int ncfg, const void* links, double* scratch,
+                       size_t scratch_bytes, tgf_obs* obs_dev, size_t obs_stride, int rec, double t, unsigned flags,
+                       void* stream) {
+    tgf_status s;
+    if ((s = check_prec(prec)) || (s = check_lat(lat, ncfg)) || (s = check_ptr(links, "links")) ||
+        (s = check_ptr(scratch, "scratch")) || (s = check_ptr(obs_dev, "obs_dev")))
+        return s;
+    Layout Ly = layout(prec, lat, ncfg);
+    if (scratch_bytes < (size_t)Ly.meas_blocks * kPartials * sizeof(double))
+        return fail(TGF_EINVAL, "scratch of %zu bytes too small (need %zu)", scratch_bytes,
+                    (size_t)Ly.meas_blocks * kPartials * sizeof(double));
+    if (rec < 0 || (ncfg > 1 && (size_t)rec >= obs_stride))
+        return fail(TGF_EINVAL, "record %d outside the stride %zu", rec, obs_stride);
+    std::vector<int> which = all_cfgs(ncfg), recs(ncfg, rec);
+    std::vector<double> ts(ncfg, t);
+    return enqueue_measure(prec, flags, lat, Ly, which, recs, ts, obs_stride, links, scratch, obs_dev,
+                           (cudaStream_t)stream);
+}
+
+tgf_status tgf_flow_records(double eps, double t_end, int measure_every, int* n_records) {
+    if (!(eps > 0) || !std::isfinite(eps)) return fail(TGF_EINVAL, "eps = %g must be positive", eps);
+    if (!(t_end >= 0) || !std::isfinite(t_end)) return fail(TGF_EINVAL, "t_end = %g must be >= 0", t_end);
+    if (measure_every < 1) return fail(TGF_EINVAL, "measure_every = %d must be >= 1", measure_every);
+    if (!n_records) return fail(TGF_EINVAL, "n_records is NULL");
+    if (t_end / eps > 1e8) return fail(TGF_EINVAL, "t_end/eps = %g steps is too many", t_end / eps);
+    int64_t n;
+    double rest;
+    flow_counts(eps, t_end, n, rest);
+    *n_records = (int)records_of(n, rest, measure_every);
+    return TGF_OK;
+}
+
+static tgf_status enqueue_flow(int prec, const tgf_lattice* lat, int ncfg, const Layout& Ly, void* w, void* w_tmp,
+                               void* accum, double* scratch, double eps, const std::vector<int64_t>& n,
+                               const std::vector<double>& rest, int measure_every, int reunit_every, unsigned flags,
+                               tgf_obs* obs, size_t obs_cap, cudaStream_t st) {
+    tgf_status s;
+    std::vector<int64_t> total(ncfg);
+    int64_t maxT = 0;
+    for (int c = 0; c < ncfg; ++c) {
+        total[c] = n[c] + (rest[c] > 0 ? 1 : 0);
+        maxT = std::max(maxT, total[c]);
+    }
+    std::vector<int> rec(ncfg, 0);
+    void* cur = w;
+    void* alt = w_tmp;
+    // configurations with nothing to integrate: one record at t = 0
+    {
+        std::vector<int> which, r;
+        std::vector<double> t;
+        for (int c = 0; c < ncfg; ++c)
+            if (total[c] == 0) { which.push_back(c); r.push_back(rec[c]++); t.push_back(0.0); }
+        if (!which.empty() &&
+            (s = enqueue_measure(prec, flags, lat, Ly, which, r, t, obs_cap, cur, scratch, obs, st)))
+            return s;
+    }
+    for (int64_t i = 0; i < maxT; ++i) {
+        std::vector<int> act, mw, mr;
+        std::vector<double> mt;
+        for (int c = 0; c < ncfg; ++c) {
+            if (i >= total[c]) continue;
+            act.push_back(c);
+            if (i % measure_every == 0) { mw.push_back(c); mr.push_back(rec[c]++); mt.push_back((double)i * eps); }
+        }
+        if (!mw.empty() && (s = enqueue_measure(prec, flags, lat, Ly, mw, mr, mt, obs_cap, cur, scratch, obs, st)))
+            return s;
+        Batch B = make_batch(lat, Ly, act, 32);
+        for (int k = 0; k < B.ncfg; ++k) {
+            const int c = act[k];
+            B.c[k].h = (i < n[c]) ? eps : rest[c];
+        }
+        const int ru = (prec != TGF_FP64 && reunit_every > 0 && (i + 1) % reunit_every == 0) ? 1 : 0;
+        launch_stage(prec, 1, 0, B, cur, alt, accum, 32, st);
+        if ((s = last_launch("stage 1"))) return s;
+        launch_stage(prec, 2, 0, B, alt, cur, accum, 32, st);
+        if ((s = last_launch("stage 2"))) return s;
+        launch_stage(prec, 3, ru, B, cur, alt, accum, 32, st);
+        if ((s = last_launch("stage 3"))) return s;
+        std::swap(cur, alt);
+        std::vector<int> fw, fr;
+        std::vector<double> ft;
+        for (int c : act)
+            if (total[c] == i + 1) { fw.push_back(c); fr.push_back(rec[c]++); ft.push_back((double)n[c] * eps + rest[c]); }
+        if (!fw.empty() && (s = enqueue_measure(prec, flags, lat, Ly, fw, fr, ft, obs_cap, cur, scratch, obs, st)))
+            return s;
+    }
+    // configurations that finished after an odd number of steps hold their field in w_tmp
+    const size_t rs = real_size(prec);
+    for (int c = 0; c < ncfg; ++c) {
+        if (total[c] % 2 == 1) {
+            const size_t off = (size_t)Ly.w_off[c] * rs;
+            const size_t bytes = (size_t)4 * reals_of(prec) * padded(sites(lat[c])) * rs;
+            TGF_CUDA(cudaMemcpyAsync((char*)w + off, (const char*)w_tmp + off, bytes, cudaMemcpyDeviceToDevice, st));
+        }
+    }
+    return TGF_OK;
+}
+
+tgf_status tgf_flow(int prec, const tgf_lattice* lat, int ncfg, void* w, void* w_tmp, void* accum, double* scratch,
+                    size_t scratch_bytes, double eps, const double* t_end, int measure_every, int reunit_every,
+                    unsigned flags, tgf_obs* obs_dev, size_t obs_cap, int* n_records, void* stream) {
+    tgf_status s;
+    if ((s = check_prec(prec)) || (s = check_lat(lat, ncfg)) || (s = check_ptr(w, "w")) ||
+        (s = check_ptr(w_tmp, "w_tmp")) || (s = check_ptr(accum, "accum")) || (s = check_ptr(scratch, "scratch")) ||
+        (s = check_ptr(obs_dev, "obs_dev")))
+        return s;
+    if (w == w_tmp) return fail(TGF_EINVAL, "w and w_tmp must be distinct buffers");
+    if (!t_end) return fail(TGF_EINVAL, "t_end is NULL");
+    if (!n_records) return fail(TGF_EINVAL, "n_records is NULL");
+    if (reunit_every < 0) return fail(TGF_EINVAL, "reunit_every = %d must be >= 0", reunit_every);
+    Layout Ly = layout(prec, lat, ncfg);
+    if (scratch_bytes < (size_t)Ly.meas_blocks * kPartials * sizeof(double))
+        return fail(TGF_EINVAL, "scratch of %zu bytes too small (need %zu)", scratch_bytes,
+                    (size_t)Ly.meas_blocks * kPartials * sizeof(double));
+    std::vector<int64_t> n(ncfg);
+    std::vector<double> rest(ncfg);
+    for (int c = 0; c < ncfg; ++c) {
+        int nr;
+        if ((s = tgf_flow_records(eps, t_end[c], measure_every, &nr))) return s;
+        if ((size_t)nr > obs_cap) return fail(TGF_EINVAL, "configuration %d needs %d records, obs_cap = %zu", c, nr, obs_cap);
+        flow_counts(eps, t_end[c], n[c], rest[c]);
+        n_records[c] = nr;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    if (flags & TGF_NO_GRAPH)
+        return enqueue_flow(prec, lat, ncfg, Ly, w, w_tmp, accum, scratch, eps, n, rest, measure_every, reunit_every,
+                            flags, obs_dev, obs_cap, st);
+
+    // ---- one CUDA graph per distinct call, cached -----------------------------------------
+    int dev = 0;
+    TGF_CUDA(cudaGetDevice(&dev));
+    std::string key;
+    auto put = [&key](const void* p, size_t b) { key.append((const char*)p, b); };
+    put(&dev, sizeof dev); put(&prec, sizeof prec); put(&ncfg, sizeof ncfg);
+    put(lat, sizeof(tgf_lattice) * ncfg);
+    put(&w, sizeof w); put(&w_tmp, sizeof w_tmp); put(&accum, sizeof accum); put(&scratch, sizeof scratch);
+    put(&eps, sizeof eps); put(t_end, sizeof(double) * ncfg);
+    put(&measure_every, sizeof measure_every); put(&reunit_every, sizeof reunit_every); put(&flags, sizeof flags);
+    put(&obs_dev, sizeof obs_dev); put(&obs_cap, sizeof obs_cap);
+
+    std::lock_guard<std::mutex> lock(g_graph_mu);
+    cudaGraphExec_t exec = nullptr;
+    for (auto it = g_graphs.begin(); it != g_graphs.end(); ++it) {
+        if (it->device == dev && it->key == key) {
+            exec = it->exec;
+            g_graphs.splice(g_graphs.begin(), g_graphs, it);
+            break;
+        }
+    }
+    if (!exec) {
+        if (dev < 0 || dev >= 64) return fail(TGF_EINVAL, "device %d out of range", dev);
+        if (!g_capture[dev]) TGF_CUDA(cudaStreamCreateWithFlags(&g_capture[dev], cudaStreamNonBlocking));
+        cudaStream_t cs = g_capture[dev];
+        TGF_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+        s = enqueue_flow(prec, lat, ncfg, Ly, w, w_tmp, accum, scratch, eps, n, rest, measure_every, reunit_every,
+                         flags, obs_dev, obs_cap, cs);
+        cudaGraph_t graph = nullptr;
+        cudaError_t ce = cudaStreamEndCapture(cs, &graph);
+        if (s) {
+            if (graph) cudaGraphDestroy(graph);
+            return s;
+        }
+        if (ce != cudaSuccess) return fail(TGF_ECUDA, "cudaStreamEndCapture: %s", cudaGetErrorString(ce));
+        ce = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (ce != cudaSuccess) return fail(TGF_ECUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(ce));
+        g_graphs.push_front(GraphEntry{key, dev, exec});
+        while (g_graphs.size() > kGraphCache) {
+            cudaGraphExecDestroy(g_graphs.back().exec);
+            g_graphs.pop_back();
+        }
+    }
+    TGF_CUDA(cudaGraphLaunch(exec, st));
+    return TGF_OK;
+}
+
+}  // extern "C"

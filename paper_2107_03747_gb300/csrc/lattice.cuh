@@ -1,0 +1,217 @@
+// lattice.cuh -- batch descriptors, device storage layouts and neighbour indexing.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "su3.cuh"
+
+namespace tgf {
+
+constexpr int kMaxCfg = 256;     // TGF_MAX_CFG
+constexpr int kSiteAlign = 32;   // Vp = V rounded up to a multiple of this
+
+enum Prec { P64 = 0, P32 = 1, P32R12 = 2 };
+
+// One configuration of a launch.  Offsets are in reals of the storage type.
+struct CfgDesc {
+    int L[4];
+    int V;            // sites
+    int Vp;           // padded plane length
+    int blk0;         // first block of this configuration in the launch
+    int rec;          // measurement record index (tgf_measure)
+    int64_t w_off;    // link storage offset (reals)
+    int64_t x_off;    // accumulator offset (reals)
+    int64_t o_off;    // observable slot (records) = cfg * obs_stride + rec
+    double h;         // step size (stages) or flow time t (measure)
+    int8_t tw[16];    // n_{mu nu} mod 3 in {0,1,2}, row-major 4x4, antisymmetric mod 3
+};
+
+// Launch descriptor passed by value as a kernel parameter; CAP = 16 or kMaxCfg keeps the
+// parameter block small for the common few-configuration launches.
+template <int CAP>
+struct BatchT {
+    int ncfg;
+    int nblk;         // total blocks of the launch
+    CfgDesc c[CAP];
+};
+using Batch = BatchT<kMaxCfg>;
+constexpr int kSmallCap = 16;
+
+// Block -> configuration by binary search over blk0 (ascending).
+template <int CAP>
+__device__ __forceinline__ int find_cfg(const BatchT<CAP>& B, int blk) {
+    int lo = 0, hi = B.ncfg - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (B.c[mid].blk0 <= blk) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+struct Site {
+    int s;        // site index
+    int x[4];     // coordinates
+    int L[4];
+    int st[4];    // strides
+};
+
+__device__ __forceinline__ void make_site(Site& p, const CfgDesc& c, int s) {
+    p.s = s;
+    p.L[0] = c.L[0]; p.L[1] = c.L[1]; p.L[2] = c.L[2]; p.L[3] = c.L[3];
+    p.st[0] = 1; p.st[1] = p.L[0]; p.st[2] = p.L[0] * p.L[1]; p.st[3] = p.st[2] * p.L[2];
+    int t = s;
+    p.x[0] = t % p.L[0]; t /= p.L[0];
+    p.x[1] = t % p.L[1]; t /= p.L[1];
+    p.x[2] = t % p.L[2];
+    p.x[3] = t / p.L[2];
+}
+
+// site index of n + d*mu_hat (d = +1 or -1), periodic
+__device__ __forceinline__ int nb(const Site& p, int s, int xmu, int mu, int d) {
+    if (d > 0) return (xmu == p.L[mu] - 1) ? s - (p.L[mu] - 1) * p.st[mu] : s + p.st[mu];
+    return (xmu == 0) ? s + (p.L[mu] - 1) * p.st[mu] : s - p.st[mu];
+}
+
+// exp(2 pi i k / 3) for k in {1, 2}
+template <class T>
+__device__ __forceinline__ void centre(int k, T& zr, T& zi) {
+    zr = T(-0.5);
+    zi = (k == 1) ? T(0.86602540378443864676) : T(-0.86602540378443864676);
+}
+
+// ---------------------------------------------------------------------------------------------
+// storage traits: load / store a link of direction mu at site s
+// ---------------------------------------------------------------------------------------------
+
+template <int P>
+struct Store;
+
+template <>
+struct Store<P64> {
+    using T = double;
+    static constexpr int reals = 18;
+    static __device__ __forceinline__ void load(const double* __restrict__ base, int Vp, int s, mat3<double>& u) {
+        const double2* q = reinterpret_cast<const double2*>(base);
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+            double2 v = __ldg(q + (size_t)k * Vp + s);
+            u.e[k / 3][k % 3] = {v.x, v.y};
+        }
+    }
+    static __device__ __forceinline__ void store(double* __restrict__ base, int Vp, int s, const mat3<double>& u) {
+        double2* q = reinterpret_cast<double2*>(base);
+#pragma unroll
+        for (int k = 0; k < 9; ++k) q[(size_t)k * Vp + s] = make_double2(u.e[k / 3][k % 3].re, u.e[k / 3][k % 3].im);
+    }
+};
+
+template <>
+struct Store<P32> {
+    using T = float;
+    static constexpr int reals = 18;
+    static __device__ __forceinline__ void load(const float* __restrict__ base, int Vp, int s, mat3<float>& u) {
+        const float4* q = reinterpret_cast<const float4*>(base);
+#pragma unroll
+        for (int g = 0; g < 4; ++g) {
+            float4 v = __ldg(q + (size_t)g * Vp + s);
+            u.e[(2 * g) / 3][(2 * g) % 3] = {v.x, v.y};
+            u.e[(2 * g + 1) / 3][(2 * g + 1) % 3] = {v.z, v.w};
+        }
+        float2 w = __ldg(reinterpret_cast<const float2*>(base + (size_t)16 * Vp) + s);
+        u.e[2][2] = {w.x, w.y};
+    }
+    static __device__ __forceinline__ void store(float* __restrict__ base, int Vp, int s, const mat3<float>& u) {
+        float4* q = reinterpret_cast<float4*>(base);
+#pragma unroll
+        for (int g = 0; g < 4; ++g)
+            q[(size_t)g * Vp + s] = make_float4(u.e[(2 * g) / 3][(2 * g) % 3].re, u.e[(2 * g) / 3][(2 * g) % 3].im,
+                                                u.e[(2 * g + 1) / 3][(2 * g + 1) % 3].re,
+                                                u.e[(2 * g + 1) / 3][(2 * g + 1) % 3].im);
+        reinterpret_cast<float2*>(base + (size_t)16 * Vp)[s] = make_float2(u.e[2][2].re, u.e[2][2].im);
+    }
+};
+
+template <>
+struct Store<P32R12> {
+    using T = float;
+    static constexpr int reals = 12;
+    static __device__ __forceinline__ void load(const float* __restrict__ base, int Vp, int s, mat3<float>& u) {
+        const float4* q = reinterpret_cast<const float4*>(base);
+#pragma unroll
+        for (int g = 0; g < 3; ++g) {
+            float4 v = __ldg(q + (size_t)g * Vp + s);
+            u.e[(2 * g) / 3][(2 * g) % 3] = {v.x, v.y};
+            u.e[(2 * g + 1) / 3][(2 * g + 1) % 3] = {v.z, v.w};
+        }
+        rebuild_row2(u);
+    }
+    static __device__ __forceinline__ void store(float* __restrict__ base, int Vp, int s, const mat3<float>& u) {
+        float4* q = reinterpret_cast<float4*>(base);
+#pragma unroll
+        for (int g = 0; g < 3; ++g)
+            q[(size_t)g * Vp + s] = make_float4(u.e[(2 * g) / 3][(2 * g) % 3].re, u.e[(2 * g) / 3][(2 * g) % 3].im,
+                                                u.e[(2 * g + 1) / 3][(2 * g + 1) % 3].re,
+                                                u.e[(2 * g + 1) / 3][(2 * g + 1) % 3].im);
+    }
+};
+
+// accumulator X: 8 reals per link as two (FP32: float4) or four (FP64: double2) planes
+template <class T>
+struct AccStore;
+
+template <>
+struct AccStore<double> {
+    static __device__ __forceinline__ void load(const double* __restrict__ base, int Vp, int s, alg8<double>& x) {
+        const double2* q = reinterpret_cast<const double2*>(base);
+#pragma unroll
+        for (int g = 0; g < 4; ++g) {
+            double2 v = q[(size_t)g * Vp + s];
+            x.v[2 * g] = v.x;
+            x.v[2 * g + 1] = v.y;
+        }
+    }
+    static __device__ __forceinline__ void store(double* __restrict__ base, int Vp, int s, const alg8<double>& x) {
+        double2* q = reinterpret_cast<double2*>(base);
+#pragma unroll
+        for (int g = 0; g < 4; ++g) q[(size_t)g * Vp + s] = make_double2(x.v[2 * g], x.v[2 * g + 1]);
+    }
+};
+
+template <>
+struct AccStore<float> {
+    static __device__ __forceinline__ void load(const float* __restrict__ base, int Vp, int s, alg8<float>& x) {
+        const float4* q = reinterpret_cast<const float4*>(base);
+#pragma unroll
+        for (int g = 0; g < 2; ++g) {
+            float4 v = q[(size_t)g * Vp + s];
+            x.v[4 * g] = v.x;
+            x.v[4 * g + 1] = v.y;
+            x.v[4 * g + 2] = v.z;
+            x.v[4 * g + 3] = v.w;
+        }
+    }
+    static __device__ __forceinline__ void store(float* __restrict__ base, int Vp, int s, const alg8<float>& x) {
+        float4* q = reinterpret_cast<float4*>(base);
+#pragma unroll
+        for (int g = 0; g < 2; ++g)
+            q[(size_t)g * Vp + s] = make_float4(x.v[4 * g], x.v[4 * g + 1], x.v[4 * g + 2], x.v[4 * g + 3]);
+    }
+};
+
+// ---------------------------------------------------------------------------------------------
+// host-side launchers (one translation unit each)
+// ---------------------------------------------------------------------------------------------
+
+void launch_stage(int prec, int stage, int reunit, const Batch& B, const void* w_in, void* w_out, void* acc,
+                  int sites_per_block, cudaStream_t st);
+void launch_measure(int prec, unsigned flags, const Batch& B, const void* w, double* partial,
+                    cudaStream_t st);
+void launch_reduce(const Batch& B, const double* partial, double* obs, cudaStream_t st);
+void launch_pack(int prec, const Batch& B, const double* canon, void* w, cudaStream_t st);
+void launch_unpack(int prec, const Batch& B, const void* w, double* canon, cudaStream_t st);
+
+constexpr int kMeasureSites = 128;  // sites (threads) per block of the measurement kernel
+constexpr int kPartials = 4;        // doubles per block partial: E, q, p, pad
+
+}  // namespace tgf

@@ -1,0 +1,195 @@
+// su3.cuh -- 3x3 complex matrix arithmetic in registers, templated on the real type.
+//
+// Products are written out entry by entry so that the compiler keeps every operand
+// in registers and contracts the multiply-adds into FMAs; no shared memory, no
+// loops that survive unrolling.
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace tgf {
+
+template <class T>
+struct cx {
+    T re, im;
+};
+
+template <class T>
+struct mat3 {
+    cx<T> e[3][3];
+};
+
+template <class T>
+__device__ __forceinline__ void set_zero(mat3<T>& a) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) a.e[i][j] = {T(0), T(0)};
+}
+
+template <class T>
+__device__ __forceinline__ void add_to(mat3<T>& a, const mat3<T>& b) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            a.e[i][j].re += b.e[i][j].re;
+            a.e[i][j].im += b.e[i][j].im;
+        }
+}
+
+// a *= (zr + i zi)
+template <class T>
+__device__ __forceinline__ void scale_cx(mat3<T>& a, T zr, T zi) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            T r = a.e[i][j].re, m = a.e[i][j].im;
+            a.e[i][j].re = r * zr - m * zi;
+            a.e[i][j].im = r * zi + m * zr;
+        }
+}
+
+// c = a b
+template <class T>
+__device__ __forceinline__ void mul_nn(mat3<T>& c, const mat3<T>& a, const mat3<T>& b) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            T re = a.e[i][0].re * b.e[0][j].re - a.e[i][0].im * b.e[0][j].im;
+            T im = a.e[i][0].re * b.e[0][j].im + a.e[i][0].im * b.e[0][j].re;
+#pragma unroll
+            for (int k = 1; k < 3; ++k) {
+                re = fma(a.e[i][k].re, b.e[k][j].re, re);
+                re = fma(-a.e[i][k].im, b.e[k][j].im, re);
+                im = fma(a.e[i][k].re, b.e[k][j].im, im);
+                im = fma(a.e[i][k].im, b.e[k][j].re, im);
+            }
+            c.e[i][j] = {re, im};
+        }
+}
+
+// c = a b^+
+template <class T>
+__device__ __forceinline__ void mul_nd(mat3<T>& c, const mat3<T>& a, const mat3<T>& b) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            // sum_k a_ik conj(b_jk)
+            T re = a.e[i][0].re * b.e[j][0].re + a.e[i][0].im * b.e[j][0].im;
+            T im = a.e[i][0].im * b.e[j][0].re - a.e[i][0].re * b.e[j][0].im;
+#pragma unroll
+            for (int k = 1; k < 3; ++k) {
+                re = fma(a.e[i][k].re, b.e[j][k].re, re);
+                re = fma(a.e[i][k].im, b.e[j][k].im, re);
+                im = fma(a.e[i][k].im, b.e[j][k].re, im);
+                im = fma(-a.e[i][k].re, b.e[j][k].im, im);
+            }
+            c.e[i][j] = {re, im};
+        }
+}
+
+// c = a^+ b
+template <class T>
+__device__ __forceinline__ void mul_dn(mat3<T>& c, const mat3<T>& a, const mat3<T>& b) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            // sum_k conj(a_ki) b_kj
+            T re = a.e[0][i].re * b.e[0][j].re + a.e[0][i].im * b.e[0][j].im;
+            T im = a.e[0][i].re * b.e[0][j].im - a.e[0][i].im * b.e[0][j].re;
+#pragma unroll
+            for (int k = 1; k < 3; ++k) {
+                re = fma(a.e[k][i].re, b.e[k][j].re, re);
+                re = fma(a.e[k][i].im, b.e[k][j].im, re);
+                im = fma(a.e[k][i].re, b.e[k][j].im, im);
+                im = fma(-a.e[k][i].im, b.e[k][j].re, im);
+            }
+            c.e[i][j] = {re, im};
+        }
+}
+
+// c += a b^+
+template <class T>
+__device__ __forceinline__ void mul_nd_acc(mat3<T>& c, const mat3<T>& a, const mat3<T>& b) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            T re = c.e[i][j].re, im = c.e[i][j].im;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                re = fma(a.e[i][k].re, b.e[j][k].re, re);
+                re = fma(a.e[i][k].im, b.e[j][k].im, re);
+                im = fma(a.e[i][k].im, b.e[j][k].re, im);
+                im = fma(-a.e[i][k].re, b.e[j][k].im, im);
+            }
+            c.e[i][j] = {re, im};
+        }
+}
+
+// c += a^+ b
+template <class T>
+__device__ __forceinline__ void mul_dn_acc(mat3<T>& c, const mat3<T>& a, const mat3<T>& b) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            T re = c.e[i][j].re, im = c.e[i][j].im;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                re = fma(a.e[k][i].re, b.e[k][j].re, re);
+                re = fma(a.e[k][i].im, b.e[k][j].im, re);
+                im = fma(a.e[k][i].re, b.e[k][j].im, im);
+                im = fma(-a.e[k][i].im, b.e[k][j].re, im);
+            }
+            c.e[i][j] = {re, im};
+        }
+}
+
+// Row 2 of an SU(3) matrix from rows 0 and 1: r2 = conj(r0 x r1).
+template <class T>
+__device__ __forceinline__ void rebuild_row2(mat3<T>& u) {
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        const int a = (j + 1) % 3, b = (j + 2) % 3;
+        // (r0_a r1_b - r0_b r1_a)^*
+        T re = u.e[0][a].re * u.e[1][b].re - u.e[0][a].im * u.e[1][b].im
+             - (u.e[0][b].re * u.e[1][a].re - u.e[0][b].im * u.e[1][a].im);
+        T im = u.e[0][a].re * u.e[1][b].im + u.e[0][a].im * u.e[1][b].re
+             - (u.e[0][b].re * u.e[1][a].im + u.e[0][b].im * u.e[1][a].re);
+        u.e[2][j] = {re, -im};
+    }
+}
+
+// The 8 real parameters of a traceless anti-Hermitian matrix
+//   X = [[ i a0,      b01,      b02 ],
+//        [ -b01^*,    i a1,     b12 ],
+//        [ -b02^*,   -b12^*,    i a2 ]],   a2 = -a0 - a1,
+// stored as {a0, a1, b01.re, b01.im, b02.re, b02.im, b12.re, b12.im}.
+template <class T>
+struct alg8 {
+    T v[8];
+};
+
+// -P_ta(M) with P_ta(M) = (M - M^+)/2 - tr(M - M^+)/6 * 1: the flow force from Omega = U Sigma.
+template <class T>
+__device__ __forceinline__ void minus_proj_ta(alg8<T>& z, const mat3<T>& m) {
+    const T third = T(1) / T(3);
+    T tr = (m.e[0][0].im + m.e[1][1].im + m.e[2][2].im) * third;
+    z.v[0] = -(m.e[0][0].im - tr);
+    z.v[1] = -(m.e[1][1].im - tr);
+    // b_jk = -(m_jk - conj(m_kj))/2
+    z.v[2] = -T(0.5) * (m.e[0][1].re - m.e[1][0].re);
+    z.v[3] = -T(0.5) * (m.e[0][1].im + m.e[1][0].im);
+    z.v[4] = -T(0.5) * (m.e[0][2].re - m.e[2][0].re);
+    z.v[5] = -T(0.5) * (m.e[0][2].im + m.e[2][0].im);
+    z.v[6] = -T(0.5) * (m.e[1][2].re - m.e[2][1].re);
+    z.v[7] = -T(0.5) * (m.e[1][2].im + m.e[2][1].im);
+}
+
+}  // namespace tgf

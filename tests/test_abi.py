@@ -1,0 +1,120 @@
+"""The C ABI without a GPU: the library builds, loads and exports every entry point of
+include/tgf.h; host-only entry points agree with the oracle; bad arguments are rejected
+before any device work."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2107_03747_gb300 import build
+
+    build.build()
+    from paper_2107_03747_gb300 import binding
+
+    return binding
+
+
+def header_functions():
+    src = open(os.path.join(ROOT, "include", "tgf.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(tgf_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = header_functions()
+    assert len(names) >= 17
+    so = C.CDLL(lib.LIB_PATH)
+    for n in names:
+        assert hasattr(so, n), n
+    assert set(names) == set(lib.EXPORTED)
+
+
+def test_version_and_status_strings(lib):
+    assert re.match(r"^\d+\.\d+\.\d+$", lib.version())
+    assert lib.status_string(0) == "ok"
+    assert lib.status_string(1) == "invalid argument"
+
+
+def test_norm_matches_oracle(lib):
+    from oracle import tgf_oracle as O
+
+    for c, Lt in [(0.3, 12), (0.1, 12), (0.4, 18), (0.3, 24)]:
+        assert lib.tgf_norm(c, Lt) == pytest.approx(O.lattice_norm(c, Lt), rel=1e-12)
+
+
+def test_lambda_matches_oracle_and_cut(lib):
+    from oracle import tgf_oracle as O
+
+    E = [0.5, 0.7, 0.9, 1.1]
+    Q = [0.2, -0.5, 0.49, 1.3]
+    lam, kept = lib.tgf_lambda(0.3, 12, 2.0, E, Q)
+    lo, ko = O.lambda_tgf(0.3, 12, 2.0, E, Q)
+    assert kept == ko == 2
+    assert lam == pytest.approx(lo, rel=1e-12)
+    assert lib.tgf_lambda(0.3, 12, 2.0, [1.0], [0.5]) == (None, 0)
+
+
+def test_flow_record_counts(lib):
+    from oracle import tgf_oracle as O
+
+    for eps, t_end, me in [(0.01, 0.18, 1), (0.01, 0.405, 1), (0.01, 0.72, 4), (0.01, 0.0, 1), (0.02, 0.1, 3)]:
+        n, rest = O.flow_steps(t_end, eps)
+        steps = n + (1 if rest > 0 else 0)
+        expect = len(range(0, steps, me)) + 1
+        assert lib.tgf_flow_records(eps, t_end, me) == expect
+
+
+def test_sizes(lib):
+    lat = lib.lattices([(4, 4, 12, 12), (2, 2, 6, 6)])
+    V = [2304, 144]
+    Vp = [2304, 160]
+    assert lib.tgf_links_bytes(lib.TGF_FP64, lat) == sum(4 * 18 * 8 * v for v in Vp)
+    assert lib.tgf_links_bytes(lib.TGF_FP32, lat) == sum(4 * 18 * 4 * v for v in Vp)
+    assert lib.tgf_links_bytes(lib.TGF_FP32_R12, lat) == sum(4 * 12 * 4 * v for v in Vp)
+    assert lib.tgf_accum_bytes(lib.TGF_FP64, lat) == sum(4 * 8 * 8 * v for v in Vp)
+    assert lib.tgf_scratch_bytes(lat) == sum((v + 127) // 128 for v in V) * 32
+    assert lib.tgf_canonical_bytes(lib.lattices([(4, 4, 12, 12)])) == 2304 * 72 * 8
+
+
+@pytest.mark.parametrize("bad", ["extent", "ncfg", "prec", "null", "align", "eps", "stage", "same"])
+def test_bad_arguments_are_rejected_before_device_work(lib, bad):
+    lat = lib.lattices([(4, 4, 12, 12)])
+    ok = 1 << 20  # a fake, aligned "device" address: never dereferenced because checks fail first
+    args = dict(prec=lib.TGF_FP64, lat=lat, n=1, w_in=ok, w_out=ok * 2, acc=ok * 3, stage=1, eps=0.01)
+    if bad == "extent":
+        args["lat"] = lib.lattices([(1, 4, 12, 12)])
+    elif bad == "ncfg":
+        args["n"] = 0
+    elif bad == "prec":
+        args["prec"] = 7
+    elif bad == "null":
+        args["w_in"] = None
+    elif bad == "align":
+        args["w_in"] = ok + 8
+    elif bad == "eps":
+        args["eps"] = float("nan")
+    elif bad == "stage":
+        args["stage"] = 4
+    elif bad == "same":
+        args["w_out"] = ok
+    s = lib._lib.tgf_stage(args["prec"], args["lat"], args["n"], args["w_in"], args["w_out"], args["acc"],
+                           args["stage"], args["eps"], 0, None)
+    assert s == lib.TGF_EINVAL
+    assert len(lib._lib.tgf_last_error()) > 0
+
+
+def test_flow_rejects_small_obs_capacity(lib):
+    lat = lib.lattices([(4, 4, 12, 12)])
+    a = 1 << 20
+    te = (C.c_double * 1)(0.18)
+    nrec = (C.c_int * 1)()
+    s = lib._lib.tgf_flow(0, lat, 1, a, 2 * a, 3 * a, 4 * a, 1 << 20, 0.01, te, 1, 0, 0, 5 * a, 3, nrec, None)
+    assert s == lib.TGF_EINVAL
+    assert b"records" in lib._lib.tgf_last_error()

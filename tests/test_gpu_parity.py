@@ -1,0 +1,301 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle, element by element.
+
+FP64 bar: 1e-12 relative on E, P, S; |dQ| <= 1e-12 max(1, |Q|); links 1e-12 absolute.
+FP32 bars: the stated FP32 tolerances below (links ~1e-5 after a step, |dE/E| <= 1e-6 on the flow).
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle import tgf_oracle as O
+from paper_2107_03747_gb300 import inputs as I
+from tests import fields as F
+
+pytestmark = pytest.mark.gpu
+
+TW = I.default_twist(1)
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+def close_obs(g, o, rel=1e-12):
+    """g: (t, E, Q, P, S) from the GPU; o: oracle dict or tuple."""
+    if isinstance(o, dict):
+        o = (g[0], o["E"], o["Q"], o["P"], o["S"])
+    assert g[0] == pytest.approx(o[0], abs=1e-12)
+    assert g[1] == pytest.approx(o[1], rel=rel, abs=1e-300)
+    assert abs(g[2] - o[2]) <= rel * max(1.0, abs(o[2]))
+    assert g[3] == pytest.approx(o[3], rel=rel)
+    assert g[4] == pytest.approx(o[4], rel=rel * 10, abs=rel * 100)
+
+
+def batch(tgf, Ls, prec="fp64", twists=None):
+    return tgf.FlowBatch(Ls, prec, twists)
+
+
+def load(tgf, Ls, fields, prec="fp64", twists=None):
+    b = batch(tgf, Ls, prec, twists)
+    b.set_links(fields)
+    return b
+
+
+# ---- layout ------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "fp32_r12"])
+def test_pack_unpack_roundtrip(tgf, prec):
+    Ls = [(4, 4, 12, 12), (3, 3, 5, 7)]
+    fields = [I.random_links(L, 20 + i, 0.7) for i, L in enumerate(Ls)]
+    b = load(tgf, Ls, fields, prec)
+    back = b.get_links()
+    for f, g in zip(fields, back):
+        if prec == "fp64":
+            assert np.array_equal(f, g)
+        elif prec == "fp32":
+            assert np.abs(f - g).max() <= 6e-8
+        else:
+            assert np.abs(f[..., :2, :] - g[..., :2, :]).max() <= 6e-8
+            assert np.abs(f[..., 2, :] - g[..., 2, :]).max() <= 5e-7  # rebuilt from rounded rows
+
+
+# ---- observables -------------------------------------------------------------------------------
+
+def test_measure_matches_oracle_fp64(tgf):
+    cases = [((4, 4, 12, 12), TW, 0), ((3, 3, 5, 7), TW, 1), ((2, 2, 6, 6), TW, 2)]
+    # a twist in three planes (including a long one) exercises every twisted leaf position
+    tw3 = np.zeros((4, 4), dtype=np.int64)
+    for a, b_, k in [(0, 1, 1), (0, 2, 2), (1, 3, 1)]:
+        tw3[a, b_], tw3[b_, a] = k, -k
+    cases.append(((4, 3, 5, 6), tw3, 3))
+    Ls = [c[0] for c in cases]
+    fields = [I.random_links(L, s, 0.6) for L, _, s in cases]
+    b = load(tgf, Ls, fields, "fp64", [tgf.twist6(c[1]) for c in cases])
+    g = b.measure(t=0.25)
+    for i, (L, tw, _) in enumerate(cases):
+        o = O.measure(fields[i], tw)
+        close_obs(g[i], o)
+        assert g[i][0] == 0.25
+
+
+def test_measure_traceless_flag(tgf):
+    L = (4, 4, 12, 12)
+    U = I.random_links(L, 5, 0.5)
+    b = load(tgf, [L], [U])
+    g = b.measure(flags=tgf.TGF_CLOVER_TRACELESS)[0]
+    close_obs(g, O.measure(U, TW, traceless=True))
+    g0 = b.measure()[0]
+    assert g0[1] != g[1]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "fp32_r12"])
+def test_twist_eater_on_gpu(tgf, prec):
+    L = (4, 4, 12, 12)
+    b = load(tgf, [L], [I.twist_eater(L)], prec)
+    g = b.measure()[0]
+    tol = 1e-14 if prec == "fp64" else 1e-6
+    assert abs(g[1]) < tol and abs(g[2]) < tol and abs(g[3] - 1) < tol
+    # the eater is a fixed point of the flow
+    obs, n = b.flow(0.05, 0.2)
+    o = obs.cpu().numpy()[0, : n[0]]
+    assert np.abs(o[:, 1]).max() < tol and np.abs(o[:, 3] - 1).max() < tol
+
+
+def test_gauge_invariance_on_gpu(tgf):
+    L = (4, 4, 12, 12)
+    U = I.random_links(L, 8, 0.5)
+    Ug = F.gauge_transform(U, F.random_gauge(L, 77))
+    b = load(tgf, [L, L], [U, Ug])
+    g = b.measure()
+    for k in range(1, 5):
+        assert g[1][k] == pytest.approx(g[0][k], rel=1e-12, abs=1e-13)
+    obs, n = b.flow(0.02, 0.1)
+    o = obs.cpu().numpy()
+    assert np.allclose(o[0, : n[0], 1:], o[1, : n[1], 1:], rtol=1e-12, atol=1e-13)
+
+
+@pytest.mark.parametrize("prec,tol", [("fp32", 2e-6), ("fp32_r12", 2e-6)])
+def test_measure_fp32_forms(tgf, prec, tol):
+    L = (4, 4, 12, 12)
+    U = I.random_links(L, 0, 0.3)
+    g = load(tgf, [L], [U], prec).measure()[0]
+    o = O.measure(U, TW)
+    assert g[1] == pytest.approx(o["E"], rel=tol)
+    assert abs(g[2] - o["Q"]) < tol * 10
+    assert g[3] == pytest.approx(o["P"], rel=tol)
+
+
+# ---- one RK3 step ------------------------------------------------------------------------------
+
+def test_three_stages_equal_one_rk3_step_fp64(tgf):
+    Ls = [(4, 4, 12, 12), (3, 3, 5, 7)]
+    fields = [I.random_links(L, 30 + i, 0.5) for i, L in enumerate(Ls)]
+    b = load(tgf, Ls, fields)
+    eps = 0.03
+    for s in (1, 2, 3):
+        b.stage(s, eps)
+    got = b.get_links()
+    for f, g in zip(fields, got):
+        ref = O.rk3_step(f, eps, TW)
+        assert np.abs(g - ref).max() < 1e-13
+
+
+def test_stage_one_is_exp_quarter_force(tgf):
+    L = (4, 4, 12, 12)
+    U = I.random_links(L, 31, 0.6)
+    b = load(tgf, [L], [U])
+    b.stage(1, 0.1)
+    ref = np.matmul(O.expm(0.025 * O.force(U, TW)), U)
+    assert np.abs(b.get_links()[0] - ref).max() < 1e-14
+
+
+def test_large_step_uses_scaling_and_squaring(tgf):
+    """eps Z with ||.||_F > 1 takes the scaled exponential path."""
+    L = (2, 2, 6, 6)
+    U = I.random_links(L, 32, 1.5)
+    b = load(tgf, [L], [U])
+    b.stage(1, 2.0)
+    ref = np.matmul(O.expm(0.5 * O.force(U, TW)), U)
+    assert np.abs(ref).max() > 0
+    assert np.abs(b.get_links()[0] - ref).max() < 1e-12
+
+
+@pytest.mark.parametrize("prec,tol", [("fp32", 3e-6), ("fp32_r12", 3e-6)])
+def test_rk3_step_fp32_forms(tgf, prec, tol):
+    L = (4, 4, 12, 12)
+    U = I.random_links(L, 33, 0.5)
+    b = load(tgf, [L], [U], prec)
+    for s in (1, 2, 3):
+        b.stage(s, 0.01, reunit=1 if s == 3 else 0)
+    g = b.get_links()[0]
+    ref = O.rk3_step(U, 0.01, TW)
+    assert np.abs(g - ref).max() < tol
+    assert np.abs(g @ O.dag(g) - np.eye(3)).max() < 1e-6
+
+
+# ---- whole flows ---------------------------------------------------------------------------------
+
+def read_golden(name):
+    rows = [l.split() for l in open(os.path.join(HERE, "golden", name)) if not l.startswith("#")]
+    return np.array([[float(x) for x in r] for r in rows])
+
+
+def test_flow_l4_matches_stored_oracle_trajectory(tgf):
+    """4x4x12x12, seed 0, amp 0.3, eps 0.01 to t = 0.18: every record against the stored oracle run."""
+    L = (4, 4, 12, 12)
+    ref = read_golden("flow_l4_seed0.txt")
+    b = load(tgf, [L], [I.random_links(L, 0, 0.3)])
+    obs, n = b.flow(0.01, 0.18)
+    o = obs.cpu().numpy()[0, : n[0]]
+    assert n[0] == len(ref) == 19
+    for g, r in zip(o, ref):
+        close_obs(g, r)
+
+
+def test_flow_final_links_match_oracle(tgf):
+    L = (2, 2, 6, 6)
+    U = I.random_links(L, 3, 0.5)
+    ref = read_golden("flow_l2_seed3.txt")
+    Uo, rec = O.flow(U, 0.02, 0.1, TW)
+    b = load(tgf, [L], [U])
+    obs, n = b.flow(0.02, 0.1)
+    o = obs.cpu().numpy()[0, : n[0]]
+    for g, r, r2 in zip(o, rec, ref):
+        close_obs(g, r)
+        close_obs(g, r2)
+    assert np.abs(b.get_links()[0] - Uo).max() < 1e-12
+
+
+def test_flow_mixed_batch_partial_steps_and_measure_every(tgf):
+    """Configurations of different sizes and end times (one with a partial last step) in one flow."""
+    Ls = [(2, 2, 6, 6), (3, 3, 9, 9), (4, 4, 12, 12), (2, 3, 4, 5)]
+    tends = [0.05, 0.045, 0.03, 0.0]
+    fields = [I.random_links(L, 40 + i, 0.5) for i, L in enumerate(Ls)]
+    b = load(tgf, Ls, fields)
+    obs, n = b.flow(0.01, tends, measure_every=2)
+    o = obs.cpu().numpy()
+    finals = b.get_links()
+    for i, (U, te) in enumerate(zip(fields, tends)):
+        Uo, rec = O.flow(U, 0.01, te, TW, measure_every=2)
+        assert n[i] == len(rec)
+        for g, r in zip(o[i, : n[i]], rec):
+            close_obs(g, r)
+        assert np.abs(finals[i] - Uo).max() < 1e-12
+
+
+def test_graph_and_direct_launches_agree_bitwise(tgf):
+    Ls = [(4, 4, 12, 12), (2, 2, 6, 6)]
+    fields = [I.random_links(L, 50 + i, 0.4) for i, L in enumerate(Ls)]
+    res = []
+    for flags in (0, tgf.TGF_NO_GRAPH, 0):
+        b = load(tgf, Ls, fields)
+        obs, n = b.flow(0.01, [0.07, 0.05], flags=flags)
+        res.append((obs.cpu().numpy().copy(), [f.copy() for f in b.get_links()]))
+    for r in res[1:]:
+        assert np.array_equal(r[0], res[0][0])
+        for a, c in zip(r[1], res[0][1]):
+            assert np.array_equal(a, c)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp32_r12"])
+def test_flow_fp32_forms_energy_error(tgf, prec):
+    """FP32 links with FP64 sums on the 4x4x12x12 flow: |dE/E| <= 1e-6 at every record."""
+    L = (4, 4, 12, 12)
+    ref = read_golden("flow_l4_seed0.txt")
+    b = load(tgf, [L], [I.random_links(L, 0, 0.3)], prec)
+    obs, n = b.flow(0.01, 0.18, reunit_every=1)
+    o = obs.cpu().numpy()[0, : n[0]]
+    rel = np.abs(o[:, 1] / ref[:, 1] - 1)
+    assert rel.max() <= 1e-6, rel.max()
+    assert np.abs(o[:, 2] - ref[:, 2]).max() < 1e-5
+
+
+def test_flow_is_reproducible_bitwise(tgf):
+    L = (4, 4, 12, 12)
+    U = I.random_links(L, 9, 0.5)
+    outs = []
+    for _ in range(2):
+        b = load(tgf, [L], [U], "fp32")
+        obs, n = b.flow(0.01, 0.05)
+        outs.append(obs.cpu().numpy())
+    assert np.array_equal(outs[0], outs[1])
+
+
+# ---- full-size workloads -------------------------------------------------------------------------
+
+def test_full_size_l16_measure_and_stage(tgf):
+    """16x16x48x48 (589,824 sites): observables and a first RK3 stage on every link against the oracle."""
+    L = (16, 16, 48, 48)
+    U = I.random_links(L, 0, 0.4)
+    b = load(tgf, [L], [U])
+    close_obs(b.measure()[0], O.measure(U, TW))
+    b.stage(1, 0.01)
+    ref = np.matmul(O.expm(0.0025 * O.force(U, TW)), U)
+    assert np.abs(b.get_links()[0] - ref).max() < 1e-14
+
+
+def test_full_size_16_configs_l8_one_step_sampled(tgf):
+    """16 configurations of 8x8x24x24 in one launch; configurations 0 and 13 checked link by link."""
+    L = (8, 8, 24, 24)
+    fields = [I.random_links(L, s, 0.3) for s in range(16)]
+    b = load(tgf, [L] * 16, fields)
+    g = b.measure()
+    for s in (0, 13):
+        close_obs(g[s], O.measure(fields[s], TW))
+    for st in (1, 2, 3):
+        b.stage(st, 0.01)
+    got = b.get_links()
+    for s in (0, 13):
+        assert np.abs(got[s] - O.rk3_step(fields[s], 0.01, TW)).max() < 1e-13
+
+
+def test_full_size_flow_properties_fp32(tgf):
+    """l/a = 16 flowed in FP32 to t = 0.5: S falls monotonically, E falls, links stay in SU(3)."""
+    L = (16, 16, 48, 48)
+    U = I.random_links(L, 1, 0.4)
+    b = load(tgf, [L], [U], "fp32")
+    obs, n = b.flow(0.01, 0.5, reunit_every=10)
+    o = obs.cpu().numpy()[0, : n[0]]
+    assert np.all(np.diff(o[:, 4]) < 0)
+    assert np.all(np.diff(o[:, 1]) < 0)
+    g = b.get_links()[0]
+    assert np.abs(g @ O.dag(g) - np.eye(3)).max() < 2e-6
