@@ -94,8 +94,10 @@ typedef struct {
 tgf_status tgf_links_bytes(int prec, const tgf_lattice *lat, int ncfg, size_t *bytes);
 /* Bytes of the RK3 accumulator X (8 reals per link in the working precision). */
 tgf_status tgf_accum_bytes(int prec, const tgf_lattice *lat, int ncfg, size_t *bytes);
-/* Bytes of the scratch buffer that tgf_measure and tgf_flow use for per-block partial sums. */
-tgf_status tgf_scratch_bytes(const tgf_lattice *lat, int ncfg, size_t *bytes);
+/* Bytes of the scratch buffer that tgf_measure and tgf_flow use: per-block FP64 partial sums
+ * and, per site, the two halves of the clover's anti-Hermitian part for the six planes plus the
+ * six twisted plaquette traces (114 reals per site in the working precision). */
+tgf_status tgf_scratch_bytes(int prec, const tgf_lattice *lat, int ncfg, size_t *bytes);
 /* Bytes of one configuration's canonical FP64 field: V * 4 * 9 * 16. */
 tgf_status tgf_canonical_bytes(const tgf_lattice *lat, size_t *bytes);
 
@@ -166,6 +168,14 @@ tgf_status tgf_lambda(double c, int Ltilde, double t, const double *E, const dou
                       double *lambda_out, int *n_kept);
 
 /* ---- diagnostics ---------------------------------------------------------------------------- */
+
+/* FMA-pipe peak of the current device in TFLOP/s (2 flops per FMA) for TGF_FP64 or TGF_FP32:
+ * the roofline denominator of the flow kernels, which are bound by vector FP arithmetic.  The
+ * paper has no counterpart; this is a measurement aid.  `sink_dev` is a caller-owned device
+ * buffer of at least blocks_per_sm * (number of SMs) * 8 bytes that the kernel may write;
+ * the call synchronises `stream`. */
+tgf_status tgf_fma_peak(int prec, void *sink_dev, int blocks_per_sm, int iters, double *tflops,
+                        void *stream);
 
 const char *tgf_last_error(void);
 const char *tgf_status_string(int status);

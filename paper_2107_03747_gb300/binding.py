@@ -13,7 +13,8 @@ import os
 import numpy as np
 
 PKG = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(PKG, "libtgf.so")
+# TGF_LIB_PATH selects another build of the same library (kernel-variant sweeps of the tuner)
+LIB_PATH = os.environ.get("TGF_LIB_PATH", os.path.join(PKG, "libtgf.so"))
 
 TGF_OK, TGF_EINVAL, TGF_ECUDA, TGF_EKERNEL, TGF_ESTATE = 0, 1, 3, 4, 6
 TGF_FP64, TGF_FP32, TGF_FP32_R12 = 0, 1, 2
@@ -47,7 +48,7 @@ _LATP = C.POINTER(tgf_lattice)
 _SIGS = {
     "tgf_links_bytes": [C.c_int, _LATP, C.c_int, C.POINTER(_SZ)],
     "tgf_accum_bytes": [C.c_int, _LATP, C.c_int, C.POINTER(_SZ)],
-    "tgf_scratch_bytes": [_LATP, C.c_int, C.POINTER(_SZ)],
+    "tgf_scratch_bytes": [C.c_int, _LATP, C.c_int, C.POINTER(_SZ)],
     "tgf_canonical_bytes": [_LATP, C.POINTER(_SZ)],
     "tgf_pack": [C.c_int, _LATP, C.c_int, _P, _P, _P],
     "tgf_unpack": [C.c_int, _LATP, C.c_int, _P, _P, _P],
@@ -59,6 +60,7 @@ _SIGS = {
                  C.c_int, C.c_uint, _P, _SZ, C.POINTER(C.c_int), _P],
     "tgf_flow_records": [C.c_double, C.c_double, C.c_int, C.POINTER(C.c_int)],
     "tgf_norm": [C.c_double, C.c_int, C.c_int, C.POINTER(C.c_double)],
+    "tgf_fma_peak": [C.c_int, _P, C.c_int, C.c_int, C.POINTER(C.c_double), _P],
     "tgf_lambda": [C.c_double, C.c_int, C.c_double, C.POINTER(C.c_double), C.POINTER(C.c_double), C.c_int,
                    C.POINTER(C.c_double), C.POINTER(C.c_int)],
 }
@@ -133,9 +135,9 @@ def tgf_accum_bytes(prec, lat) -> int:
     return out.value
 
 
-def tgf_scratch_bytes(lat) -> int:
+def tgf_scratch_bytes(prec, lat) -> int:
     out = _SZ()
-    _check(_lib.tgf_scratch_bytes(lat, len(lat), C.byref(out)))
+    _check(_lib.tgf_scratch_bytes(prec, lat, len(lat), C.byref(out)))
     return out.value
 
 
@@ -195,6 +197,17 @@ def tgf_flow(prec, lat, w, w_tmp, accum, scratch, eps, t_end, obs_dev, obs_cap, 
     return list(nrec)
 
 
+def tgf_fma_peak(prec, blocks_per_sm=8, iters=4096, stream=None) -> float:
+    """Measured FMA-pipe peak (TFLOP/s) of the current device for TGF_FP32 or TGF_FP64."""
+    import torch
+
+    nsm = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    sink = torch.empty(nsm * blocks_per_sm, dtype=torch.float64, device="cuda")
+    out = C.c_double()
+    _check(_lib.tgf_fma_peak(prec, _ptr(sink), blocks_per_sm, iters, C.byref(out), _stream(stream)))
+    return out.value
+
+
 def tgf_norm(c, Lt, N=3) -> float:
     out = C.c_double()
     _check(_lib.tgf_norm(c, Lt, N, C.byref(out)))
@@ -237,7 +250,8 @@ class FlowBatch:
         self.links = torch.empty(nb, dtype=torch.uint8, device=self.device)
         self.links_tmp = torch.empty(nb, dtype=torch.uint8, device=self.device)
         self.accum = torch.empty(tgf_accum_bytes(self.prec, self.lat), dtype=torch.uint8, device=self.device)
-        self.scratch = torch.empty(tgf_scratch_bytes(self.lat), dtype=torch.uint8, device=self.device)
+        self.scratch = torch.empty(tgf_scratch_bytes(self.prec, self.lat), dtype=torch.uint8,
+                                   device=self.device)
 
     @property
     def ncfg(self):

@@ -77,27 +77,35 @@ void twist_table(const tgf_lattice& l, int8_t tw[16]) {
 }
 
 struct Layout {
-    std::vector<int64_t> w_off, x_off, c_off;  // reals / reals / canonical doubles
-    std::vector<int64_t> meas_blk0;            // first measure block of each config in a full launch
-    int64_t w_total = 0, x_total = 0, meas_blocks = 0;
+    std::vector<int64_t> w_off, x_off, c_off, m_off;  // reals / reals / canonical doubles / reals
+    std::vector<int64_t> meas_blk0;                   // first measure block of each config in a full launch
+    int64_t w_total = 0, x_total = 0, m_total = 0, meas_blocks = 0;
+    // scratch: [partials: meas_blocks x kPartials doubles][pad to 256 B][clover halves: m_total reals]
+    size_t partial_bytes() const { return ((size_t)meas_blocks * kPartials * sizeof(double) + 255) / 256 * 256; }
+    size_t scratch_bytes(int prec) const;
 };
+
+size_t Layout::scratch_bytes(int prec) const { return partial_bytes() + (size_t)m_total * real_size(prec); }
 
 Layout layout(int prec, const tgf_lattice* lat, int ncfg) {
     Layout L;
-    int64_t w = 0, x = 0, cc = 0, mb = 0;
+    int64_t w = 0, x = 0, cc = 0, mb = 0, m = 0;
     for (int c = 0; c < ncfg; ++c) {
         int64_t V = sites(lat[c]), Vp = padded(V);
         L.w_off.push_back(w);
         L.x_off.push_back(x);
         L.c_off.push_back(cc);
+        L.m_off.push_back(m);
         L.meas_blk0.push_back(mb);
         w += 4 * (int64_t)reals_of(prec) * Vp;
         x += 4 * 8 * Vp;
         cc += V * 72;
+        m += (int64_t)kClovReals * Vp;
         mb += (V + kMeasureSites - 1) / kMeasureSites;
     }
     L.w_total = w;
     L.x_total = x;
+    L.m_total = m;
     L.meas_blocks = mb;
     return L;
 }
@@ -111,12 +119,15 @@ Batch make_batch(const tgf_lattice* lat, const Layout& Ly, const std::vector<int
         const int c = which[i];
         CfgDesc& d = B.c[i];
         for (int mu = 0; mu < 4; ++mu) d.L[mu] = lat[c].L[mu];
+        d.st[0] = 1;
+        for (int mu = 1; mu < 4; ++mu) d.st[mu] = d.st[mu - 1] * d.L[mu - 1];
         d.V = (int)sites(lat[c]);
         d.Vp = (int)padded(d.V);
         d.blk0 = blk;
         d.rec = 0;
         d.w_off = Ly.w_off[c];
         d.x_off = Ly.x_off[c];
+        d.m_off = Ly.m_off[c];
         d.o_off = 0;
         d.h = 0.0;
         twist_table(lat[c], d.tw);
@@ -138,21 +149,34 @@ tgf_status last_launch(const char* what) {
     return TGF_OK;
 }
 
-// measure + reduce over `which`, record r_c at time t_c
-tgf_status enqueue_measure(int prec, unsigned flags, const tgf_lattice* lat, const Layout& Ly,
-                           const std::vector<int>& which, const std::vector<int>& rec, const std::vector<double>& t,
-                           size_t obs_stride, const void* w, double* scratch, tgf_obs* obs, cudaStream_t st) {
+void* clover_base(void* scratch, const Layout& Ly) { return (char*)scratch + Ly.partial_bytes(); }
+
+// clover-sum + reduce over `which` (halves already written), record r_c at time t_c
+tgf_status enqueue_sum(int prec, unsigned flags, const tgf_lattice* lat, const Layout& Ly,
+                       const std::vector<int>& which, const std::vector<int>& rec, const std::vector<double>& t,
+                       size_t obs_stride, double* scratch, tgf_obs* obs, cudaStream_t st) {
     Batch B = make_batch(lat, Ly, which, kMeasureSites);
     for (int i = 0; i < B.ncfg; ++i) {
         B.c[i].rec = rec[i];
         B.c[i].h = t[i];
         B.c[i].o_off = (int64_t)which[i] * (int64_t)obs_stride + rec[i];
     }
-    launch_measure(prec, flags, B, w, scratch, st);
-    tgf_status s = last_launch("measure");
+    launch_clover_sum(prec, flags, B, clover_base(scratch, Ly), scratch, st);
+    tgf_status s = last_launch("clover sum");
     if (s) return s;
     launch_reduce(B, scratch, reinterpret_cast<double*>(obs), st);
     return last_launch("reduce");
+}
+
+// full measurement of `which` from the field w: clover halves, their sum, the reduction
+tgf_status enqueue_measure(int prec, unsigned flags, const tgf_lattice* lat, const Layout& Ly,
+                           const std::vector<int>& which, const std::vector<int>& rec, const std::vector<double>& t,
+                           size_t obs_stride, const void* w, double* scratch, tgf_obs* obs, cudaStream_t st) {
+    Batch B = make_batch(lat, Ly, which, 32);
+    launch_stage(prec, 1, 2, 0, B, w, nullptr, nullptr, clover_base(scratch, Ly), st);
+    tgf_status s = last_launch("clover halves");
+    if (s) return s;
+    return enqueue_sum(prec, flags, lat, Ly, which, rec, t, obs_stride, scratch, obs, st);
 }
 
 tgf_status check_ptr(const void* p, const char* name) {
@@ -219,11 +243,11 @@ tgf_status tgf_accum_bytes(int prec, const tgf_lattice* lat, int ncfg, size_t* b
     return TGF_OK;
 }
 
-tgf_status tgf_scratch_bytes(const tgf_lattice* lat, int ncfg, size_t* bytes) {
+tgf_status tgf_scratch_bytes(int prec, const tgf_lattice* lat, int ncfg, size_t* bytes) {
     tgf_status s;
-    if ((s = check_lat(lat, ncfg))) return s;
+    if ((s = check_prec(prec)) || (s = check_lat(lat, ncfg))) return s;
     if (!bytes) return fail(TGF_EINVAL, "bytes is NULL");
-    *bytes = (size_t)layout(TGF_FP64, lat, ncfg).meas_blocks * kPartials * sizeof(double);
+    *bytes = layout(prec, lat, ncfg).scratch_bytes(prec);
     return TGF_OK;
 }
 
@@ -321,7 +345,7 @@ tgf_status tgf_stage(int prec, const tgf_lattice* lat, int ncfg, const void* w_i
     Layout Ly = layout(prec, lat, ncfg);
     Batch B = make_batch(lat, Ly, all_cfgs(ncfg), 32);
     for (int i = 0; i < ncfg; ++i) B.c[i].h = eps;
-    launch_stage(prec, stage, reunit, B, w_in, w_out, accum, 32, (cudaStream_t)stream);
+    launch_stage(prec, stage, 0, reunit, B, w_in, w_out, accum, nullptr, (cudaStream_t)stream);
     return last_launch("stage");
 }
 
@@ -333,9 +357,8 @@ tgf_status tgf_measure(int prec, const tgf_lattice* lat, int ncfg, const void* l
         (s = check_ptr(scratch, "scratch")) || (s = check_ptr(obs_dev, "obs_dev")))
         return s;
     Layout Ly = layout(prec, lat, ncfg);
-    if (scratch_bytes < (size_t)Ly.meas_blocks * kPartials * sizeof(double))
-        return fail(TGF_EINVAL, "scratch of %zu bytes too small (need %zu)", scratch_bytes,
-                    (size_t)Ly.meas_blocks * kPartials * sizeof(double));
+    if (scratch_bytes < Ly.scratch_bytes(prec))
+        return fail(TGF_EINVAL, "scratch of %zu bytes too small (need %zu)", scratch_bytes, Ly.scratch_bytes(prec));
     if (rec < 0 || (ncfg > 1 && (size_t)rec >= obs_stride))
         return fail(TGF_EINVAL, "record %d outside the stride %zu", rec, obs_stride);
     std::vector<int> which = all_cfgs(ncfg), recs(ncfg, rec);
@@ -389,19 +412,20 @@ static tgf_status enqueue_flow(int prec, const tgf_lattice* lat, int ncfg, const
             act.push_back(c);
             if (i % measure_every == 0) { mw.push_back(c); mr.push_back(rec[c]++); mt.push_back((double)i * eps); }
         }
-        if (!mw.empty() && (s = enqueue_measure(prec, flags, lat, Ly, mw, mr, mt, obs_cap, cur, scratch, obs, st)))
-            return s;
+        // every active configuration starts at step 0, so either all of them are measured now or none
+        const int mode1 = mw.empty() ? 0 : 1;
         Batch B = make_batch(lat, Ly, act, 32);
         for (int k = 0; k < B.ncfg; ++k) {
             const int c = act[k];
             B.c[k].h = (i < n[c]) ? eps : rest[c];
         }
         const int ru = (prec != TGF_FP64 && reunit_every > 0 && (i + 1) % reunit_every == 0) ? 1 : 0;
-        launch_stage(prec, 1, 0, B, cur, alt, accum, 32, st);
+        launch_stage(prec, 1, mode1, 0, B, cur, alt, accum, clover_base(scratch, Ly), st);
         if ((s = last_launch("stage 1"))) return s;
-        launch_stage(prec, 2, 0, B, alt, cur, accum, 32, st);
+        if (mode1 && (s = enqueue_sum(prec, flags, lat, Ly, mw, mr, mt, obs_cap, scratch, obs, st))) return s;
+        launch_stage(prec, 2, 0, 0, B, alt, cur, accum, nullptr, st);
         if ((s = last_launch("stage 2"))) return s;
-        launch_stage(prec, 3, ru, B, cur, alt, accum, 32, st);
+        launch_stage(prec, 3, 0, ru, B, cur, alt, accum, nullptr, st);
         if ((s = last_launch("stage 3"))) return s;
         std::swap(cur, alt);
         std::vector<int> fw, fr;
@@ -436,9 +460,8 @@ tgf_status tgf_flow(int prec, const tgf_lattice* lat, int ncfg, void* w, void* w
     if (!n_records) return fail(TGF_EINVAL, "n_records is NULL");
     if (reunit_every < 0) return fail(TGF_EINVAL, "reunit_every = %d must be >= 0", reunit_every);
     Layout Ly = layout(prec, lat, ncfg);
-    if (scratch_bytes < (size_t)Ly.meas_blocks * kPartials * sizeof(double))
-        return fail(TGF_EINVAL, "scratch of %zu bytes too small (need %zu)", scratch_bytes,
-                    (size_t)Ly.meas_blocks * kPartials * sizeof(double));
+    if (scratch_bytes < Ly.scratch_bytes(prec))
+        return fail(TGF_EINVAL, "scratch of %zu bytes too small (need %zu)", scratch_bytes, Ly.scratch_bytes(prec));
     std::vector<int64_t> n(ncfg);
     std::vector<double> rest(ncfg);
     for (int c = 0; c < ncfg; ++c) {

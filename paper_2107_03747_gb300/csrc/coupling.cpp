@@ -1,12 +1,42 @@
 // coupling.cpp -- host-side lattice normalisation N(c, Lt) (eq. latt_norm) and the coupling
 // lambda_TGF (eq. lambdat_latt) from the measured E and Q of an ensemble.
 #include <cmath>
+#include <map>
+#include <mutex>
+#include <tuple>
 #include <vector>
 
 #include "../../include/tgf.h"
 
+namespace {
+// N(c, Lt) depends only on (c, Lt, N): computed once per process (O(Lt^4) host work).
+std::mutex g_norm_mu;
+std::map<std::tuple<double, int, int>, double> g_norm_cache;
+}  // namespace
+
+static tgf_status norm_uncached(double c, int Lt, int N, double* norm_out);
+
 extern "C" tgf_status tgf_norm(double c, int Lt, int N, double* norm_out) {
     if (!(c > 0) || !std::isfinite(c) || Lt < 2 || Lt > 512 || N < 2 || !norm_out) return TGF_EINVAL;
+    const auto key = std::make_tuple(c, Lt, N);
+    {
+        std::lock_guard<std::mutex> lk(g_norm_mu);
+        auto it = g_norm_cache.find(key);
+        if (it != g_norm_cache.end()) {
+            *norm_out = it->second;
+            return TGF_OK;
+        }
+    }
+    double v;
+    tgf_status s = norm_uncached(c, Lt, N, &v);
+    if (s != TGF_OK) return s;
+    std::lock_guard<std::mutex> lk(g_norm_mu);
+    g_norm_cache[key] = v;
+    *norm_out = v;
+    return TGF_OK;
+}
+
+static tgf_status norm_uncached(double c, int Lt, int N, double* norm_out) {
     const double pi = 3.14159265358979323846;
     // per-component tables: qhat_mu^2 = 4 sin^2(q/2), sin^2(q), cos^2(q/2) with q = 2 pi n / Lt
     std::vector<double> qh2(Lt), s2(Lt), c2(Lt);

@@ -16,6 +16,7 @@ enum Prec { P64 = 0, P32 = 1, P32R12 = 2 };
 // One configuration of a launch.  Offsets are in reals of the storage type.
 struct CfgDesc {
     int L[4];
+    int st[4];        // strides 1, L0, L0 L1, L0 L1 L2
     int V;            // sites
     int Vp;           // padded plane length
     int blk0;         // first block of this configuration in the launch
@@ -23,6 +24,7 @@ struct CfgDesc {
     int64_t w_off;    // link storage offset (reals)
     int64_t x_off;    // accumulator offset (reals)
     int64_t o_off;    // observable slot (records) = cfg * obs_stride + rec
+    int64_t m_off;    // clover-halves offset in the scratch buffer (reals of the storage type)
     double h;         // step size (stages) or flow time t (measure)
     int8_t tw[16];    // n_{mu nu} mod 3 in {0,1,2}, row-major 4x4, antisymmetric mod 3
 };
@@ -49,29 +51,22 @@ __device__ __forceinline__ int find_cfg(const BatchT<CAP>& B, int blk) {
     return lo;
 }
 
-struct Site {
-    int s;        // site index
-    int x[4];     // coordinates
-    int L[4];
-    int st[4];    // strides
-};
-
-__device__ __forceinline__ void make_site(Site& p, const CfgDesc& c, int s) {
-    p.s = s;
-    p.L[0] = c.L[0]; p.L[1] = c.L[1]; p.L[2] = c.L[2]; p.L[3] = c.L[3];
-    p.st[0] = 1; p.st[1] = p.L[0]; p.st[2] = p.L[0] * p.L[1]; p.st[3] = p.st[2] * p.L[2];
+// The four coordinates of a site packed in 16-bit fields of one 64-bit register; extents and
+// strides are read from the launch descriptor (parameter bank), so a direction chosen at run
+// time costs a shift, not a local-memory array access.
+__device__ __forceinline__ uint64_t pack_coords(const CfgDesc& c, int s) {
     int t = s;
-    p.x[0] = t % p.L[0]; t /= p.L[0];
-    p.x[1] = t % p.L[1]; t /= p.L[1];
-    p.x[2] = t % p.L[2];
-    p.x[3] = t / p.L[2];
+    const uint64_t x0 = (uint64_t)(t % c.L[0]); t /= c.L[0];
+    const uint64_t x1 = (uint64_t)(t % c.L[1]); t /= c.L[1];
+    const uint64_t x2 = (uint64_t)(t % c.L[2]);
+    const uint64_t x3 = (uint64_t)(t / c.L[2]);
+    return x0 | (x1 << 16) | (x2 << 32) | (x3 << 48);
 }
+__device__ __forceinline__ int coord(uint64_t xp, int d) { return (int)((xp >> (16 * d)) & 0xFFFFu); }
 
-// site index of n + d*mu_hat (d = +1 or -1), periodic
-__device__ __forceinline__ int nb(const Site& p, int s, int xmu, int mu, int d) {
-    if (d > 0) return (xmu == p.L[mu] - 1) ? s - (p.L[mu] - 1) * p.st[mu] : s + p.st[mu];
-    return (xmu == 0) ? s + (p.L[mu] - 1) * p.st[mu] : s - p.st[mu];
-}
+// site index of n +- one step along a direction with coordinate x, extent L, stride st (periodic)
+__device__ __forceinline__ int step_p(int s, int x, int L, int st) { return x == L - 1 ? s - (L - 1) * st : s + st; }
+__device__ __forceinline__ int step_m(int s, int x, int L, int st) { return x == 0 ? s + (L - 1) * st : s - st; }
 
 // exp(2 pi i k / 3) for k in {1, 2}
 template <class T>
@@ -203,15 +198,18 @@ struct AccStore<float> {
 // host-side launchers (one translation unit each)
 // ---------------------------------------------------------------------------------------------
 
-void launch_stage(int prec, int stage, int reunit, const Batch& B, const void* w_in, void* w_out, void* acc,
-                  int sites_per_block, cudaStream_t st);
-void launch_measure(int prec, unsigned flags, const Batch& B, const void* w, double* partial,
-                    cudaStream_t st);
+// mode: 0 = RK3 stage only; 1 = stage and clover halves of the input field; 2 = halves only
+void launch_stage(int prec, int stage, int mode, int reunit, const Batch& B, const void* w_in, void* w_out,
+                  void* acc, void* clov, cudaStream_t st);
+void launch_clover_sum(int prec, unsigned flags, const Batch& B, const void* clov, double* partial,
+                       cudaStream_t st);
 void launch_reduce(const Batch& B, const double* partial, double* obs, cudaStream_t st);
 void launch_pack(int prec, const Batch& B, const double* canon, void* w, cudaStream_t st);
 void launch_unpack(int prec, const Batch& B, const void* w, double* canon, cudaStream_t st);
 
 constexpr int kMeasureSites = 128;  // sites (threads) per block of the measurement kernel
 constexpr int kPartials = 4;        // doubles per block partial: E, q, p, pad
+// clover scratch per site: 6 planes x 2 halves x 9 reals (anti-Hermitian parts) + 6 plaquette traces
+constexpr int kClovReals = 6 * 2 * 9 + 6;
 
 }  // namespace tgf

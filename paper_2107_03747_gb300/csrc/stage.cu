@@ -52,70 +52,139 @@ __device__ __forceinline__ void reunitarize(mat3<T>& u) {
         for (int j = 0; j < 3; ++j) u.e[i][j] = {(T)d.e[i][j].re, (T)d.e[i][j].im};
 }
 
-template <int P, int STAGE, int SPB, int CAP>
-__global__ void __launch_bounds__(4 * SPB)
+// resident blocks per SM the register allocation must allow: FP32 forms at most 128 registers
+// per thread (4 blocks of 128 threads), FP64 at most 255 (2 blocks)
+#ifndef TGF_STAGE_MINB32
+#define TGF_STAGE_MINB32 4
+#endif
+template <int P>
+constexpr int stage_min_blocks() { return P == P64 ? 2 : TGF_STAGE_MINB32; }
+
+// Plane index of (mu, nu), mu < nu, in the order 01, 23, 02, 13, 03, 12 (consecutive planes
+// pair up in the topological charge); -1 for mu >= nu.
+__constant__ int8_t c_plane_of[4][4] = {{-1, 0, 2, 4}, {-1, -1, 5, 3}, {-1, -1, -1, 1}, {-1, -1, -1, -1}};
+
+// The anti-Hermitian part D - D^+ of a 3x3 matrix as 9 reals (2 Im D_jj; D_jk - conj(D_kj), j<k),
+// written to 9 component planes of length Vp.
+template <class T>
+__device__ __forceinline__ void store_ah(T* __restrict__ p, int Vp, int s, const mat3<T>& d) {
+    p[0 * (size_t)Vp + s] = T(2) * d.e[0][0].im;
+    p[1 * (size_t)Vp + s] = T(2) * d.e[1][1].im;
+    p[2 * (size_t)Vp + s] = T(2) * d.e[2][2].im;
+    p[3 * (size_t)Vp + s] = d.e[0][1].re - d.e[1][0].re;
+    p[4 * (size_t)Vp + s] = d.e[0][1].im + d.e[1][0].im;
+    p[5 * (size_t)Vp + s] = d.e[0][2].re - d.e[2][0].re;
+    p[6 * (size_t)Vp + s] = d.e[0][2].im + d.e[2][0].im;
+    p[7 * (size_t)Vp + s] = d.e[1][2].re - d.e[2][1].re;
+    p[8 * (size_t)Vp + s] = d.e[1][2].im + d.e[2][1].im;
+}
+
+// MODE 0: the RK3 stage.  MODE 1: the stage, and from the same staples of the input field the
+// clover halves used by the measurement.  MODE 2: the clover halves only.
+//
+// Clover from staples.  With F, B the forward and backward twisted staples of link U_mu(n) in
+// direction nu (below), the four leaves of eq. (gmunu) are L1 = U F, L2 = B^+ U^+ (both from
+// link (n, mu)) and L3 = F' U', L4 = U'^+ B'^+ (from link (n - mu, mu), primed), so
+//   C - C^+ = [D1 - D1^+] + [D2 - D2^+],  D1 = U (F - B) at n,  D2 = (F' - B') U' carried to n.
+// Thread (n, mu) writes D1 - D1^+ to site n and D (F - B) U - h.c. to site n + mu, for nu > mu,
+// plus Re Tr(U F) (the twisted plaquette at n).
+template <int P, int STAGE, int MODE, int SPB, int CAP>
+__global__ void __launch_bounds__(4 * SPB, stage_min_blocks<P>())
 k_stage(const __grid_constant__ BatchT<CAP> B, const typename Store<P>::T* __restrict__ w_in,
-        typename Store<P>::T* __restrict__ w_out, typename Store<P>::T* __restrict__ acc, int reunit) {
+        typename Store<P>::T* __restrict__ w_out, typename Store<P>::T* __restrict__ acc,
+        typename Store<P>::T* __restrict__ clov, int reunit) {
     using T = typename Store<P>::T;
     using S = Store<P>;
     constexpr int R = S::reals;
     constexpr int WPD = SPB / 32;  // warps per direction
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int mu = warp / WPD;
+    if (MODE == 2 && mu == 3) return;  // no plane (3, nu) with nu > 3
 
     for (int blk = blockIdx.x; blk < B.nblk; blk += gridDim.x) {
         const int ci = find_cfg(B, blk);
         const CfgDesc& c = B.c[ci];
         const int s = (blk - c.blk0) * SPB + (warp % WPD) * 32 + lane;
         if (s >= c.V) continue;
-        Site p;
-        make_site(p, c, s);
+        const uint64_t xp = pack_coords(c, s);
         const int Vp = c.Vp;
         const T* base = w_in + c.w_off;
         auto link = [&](int dir, int site, mat3<T>& u) { S::load(base + (size_t)dir * R * Vp, Vp, site, u); };
+        const int xm = coord(xp, mu), Lm = c.L[mu], Sm = c.st[mu];
+        const int s_mp = step_p(s, xm, Lm, Sm);
 
         mat3<T> sig, a, b, t;
-        set_zero(sig);
-        const int smu_p = nb(p, s, p.x[mu], mu, +1);
-#pragma unroll
+        if (MODE != 2) set_zero(sig);
+#pragma unroll 1
         for (int dn = 1; dn < 4; ++dn) {
             const int nu = (mu + dn) & 3;
-            const int snu_p = nb(p, s, p.x[nu], nu, +1);
-            const int snu_m = nb(p, s, p.x[nu], nu, -1);
+            const bool clover = MODE != 0 && nu > mu;
+            if (MODE == 2 && !clover) continue;
+            const int xn = coord(xp, nu), Ln = c.L[nu], Sn = c.st[nu];
+            const int s_np = step_p(s, xn, Ln, Sn);
+            const int s_nm = step_m(s, xn, Ln, Sn);
+            const int s_mp_nm = step_p(s_nm, xm, Lm, Sm);
             const int k = c.tw[mu * 4 + nu];
-            // forward staple Z*_{mu nu}(n) U_nu(n+mu) U_mu(n+nu)^+ U_nu(n)^+
-            link(nu, smu_p, a);
-            link(mu, snu_p, b);
+            T zr = T(1), zi = T(0);
+            if (k != 0) centre<T>(k, zr, zi);
+            // forward staple F = Z*_{mu nu}(n) U_nu(n+mu) U_mu(n+nu)^+ U_nu(n)^+
+            link(nu, s_mp, a);
+            link(mu, s_np, b);
             mul_nd(t, a, b);
             link(nu, s, a);
-            if (k != 0 && p.x[mu] == 0 && p.x[nu] == 0) {
-                mul_nd(b, t, a);
-                T zr, zi;
-                centre<T>(k, zr, zi);
-                scale_cx(b, zr, -zi);
-                add_to(sig, b);
+            const bool tw_f = k != 0 && xm == 0 && xn == 0;
+            mat3<T> f;
+            if (clover || tw_f) {
+                mul_nd(f, t, a);
+                if (tw_f) scale_cx(f, zr, -zi);
+                if (MODE != 2) add_to(sig, f);
             } else {
                 mul_nd_acc(sig, t, a);
             }
-            // backward staple Z_{mu nu}(n-nu) U_nu(n+mu-nu)^+ U_mu(n-nu)^+ U_nu(n-nu)
-            const int smu_p_nu_m = nb(p, snu_m, p.x[mu], mu, +1);
-            link(mu, snu_m, a);
-            link(nu, smu_p_nu_m, b);
+            // backward staple B = Z_{mu nu}(n-nu) U_nu(n+mu-nu)^+ U_mu(n-nu)^+ U_nu(n-nu)
+            link(mu, s_nm, a);
+            link(nu, s_mp_nm, b);
             mul_nn(t, a, b);
-            link(nu, snu_m, a);
-            if (k != 0 && p.x[mu] == 0 && p.x[nu] == 1) {
+            link(nu, s_nm, a);
+            const bool tw_b = k != 0 && xm == 0 && xn == 1;
+            if (clover || tw_b) {
                 mul_dn(b, t, a);
-                T zr, zi;
-                centre<T>(k, zr, zi);
-                scale_cx(b, zr, zi);
-                add_to(sig, b);
+                if (tw_b) scale_cx(b, zr, zi);
+                if (MODE != 2) add_to(sig, b);
             } else {
                 mul_dn_acc(sig, t, a);
             }
+            if (clover) {
+                const int pl = c_plane_of[mu][nu];
+                T* cb = clov + c.m_off;
+                link(mu, s, a);  // U = U_mu(n)
+                // Re Tr(U F): the twisted plaquette Z* P_{mu nu}(n)
+                T rt = T(0);
+#pragma unroll
+                for (int i = 0; i < 3; ++i)
+#pragma unroll
+                    for (int j = 0; j < 3; ++j)
+                        rt += a.e[i][j].re * f.e[j][i].re - a.e[i][j].im * f.e[j][i].im;
+                cb[(size_t)(108 + pl) * Vp + s] = rt;
+                // K = F - B; D1 = U K (site n), D2 = K U (site n + mu)
+#pragma unroll
+                for (int i = 0; i < 3; ++i)
+#pragma unroll
+                    for (int j = 0; j < 3; ++j) {
+                        f.e[i][j].re -= b.e[i][j].re;
+                        f.e[i][j].im -= b.e[i][j].im;
+                    }
+                mul_nn(t, a, f);
+                store_ah(cb + (size_t)(pl * 2 + 0) * 9 * Vp, Vp, s, t);
+                mul_nn(t, f, a);
+                store_ah(cb + (size_t)(pl * 2 + 1) * 9 * Vp, Vp, s_mp, t);
+            }
         }
+        if (MODE == 2) continue;
         // Omega = U_mu(n) Sigma, Z = -P_ta(Omega)
-        link(mu, s, a);
-        mul_nn(t, a, sig);
+        mat3<T> u;
+        link(mu, s, u);
+        mul_nn(t, u, sig);
         alg8<T> z;
         minus_proj_ta(z, t);
         const T h = (T)c.h;
@@ -137,46 +206,58 @@ k_stage(const __grid_constant__ BatchT<CAP> B, const typename Store<P>::T* __res
             for (int i = 0; i < 8; ++i) x.v[i] = T(0.75) * h * z.v[i] - x.v[i];
         }
         expm_su3(b, x);
-        mul_nn(t, b, a);
+        mul_nn(t, b, u);
         if (STAGE == 3 && P != P64 && reunit) reunitarize(t);
         S::store(w_out + c.w_off + (size_t)mu * R * Vp, Vp, s, t);
     }
 }
 
-template <int P, int STAGE, int SPB, int CAP>
-static void launch_cap(const Batch& B, const void* w_in, void* w_out, void* acc, int reunit, cudaStream_t st) {
+template <int P, int STAGE, int MODE, int CAP>
+static void launch_cap(const Batch& B, const void* w_in, void* w_out, void* acc, void* clov, int reunit,
+                       cudaStream_t st) {
     using T = typename Store<P>::T;
-    BatchT<CAP> b;
-    b.ncfg = B.ncfg;
-    b.nblk = B.nblk;
-    for (int i = 0; i < B.ncfg; ++i) b.c[i] = B.c[i];
-    k_stage<P, STAGE, SPB, CAP><<<B.nblk, 4 * SPB, 0, st>>>(b, (const T*)w_in, (T*)w_out, (T*)acc, reunit);
-}
-
-template <int P, int STAGE, int SPB>
-static void launch_p(const Batch& B, const void* w_in, void* w_out, void* acc, int reunit, cudaStream_t st) {
-    if (B.ncfg <= kSmallCap)
-        launch_cap<P, STAGE, SPB, kSmallCap>(B, w_in, w_out, acc, reunit, st);
-    else
-        launch_cap<P, STAGE, SPB, kMaxCfg>(B, w_in, w_out, acc, reunit, st);
-}
-
-template <int P>
-static void launch_stage_p(int stage, int reunit, const Batch& B, const void* w_in, void* w_out, void* acc,
-                           cudaStream_t st) {
-    switch (stage) {
-        case 1: launch_p<P, 1, 32>(B, w_in, w_out, acc, reunit, st); break;
-        case 2: launch_p<P, 2, 32>(B, w_in, w_out, acc, reunit, st); break;
-        default: launch_p<P, 3, 32>(B, w_in, w_out, acc, reunit, st); break;
+    constexpr int SPB = 32;
+    if constexpr (CAP == kMaxCfg) {
+        k_stage<P, STAGE, MODE, SPB, kMaxCfg><<<B.nblk, 4 * SPB, 0, st>>>(B, (const T*)w_in, (T*)w_out, (T*)acc,
+                                                                          (T*)clov, reunit);
+    } else {
+        BatchT<CAP> b;
+        b.ncfg = B.ncfg;
+        b.nblk = B.nblk;
+        for (int i = 0; i < B.ncfg; ++i) b.c[i] = B.c[i];
+        k_stage<P, STAGE, MODE, SPB, CAP><<<B.nblk, 4 * SPB, 0, st>>>(b, (const T*)w_in, (T*)w_out, (T*)acc,
+                                                                      (T*)clov, reunit);
     }
 }
 
-void launch_stage(int prec, int stage, int reunit, const Batch& B, const void* w_in, void* w_out, void* acc,
-                  int sites_per_block, cudaStream_t st) {
-    (void)sites_per_block;
-    if (prec == P64) launch_stage_p<P64>(stage, reunit, B, w_in, w_out, acc, st);
-    else if (prec == P32) launch_stage_p<P32>(stage, reunit, B, w_in, w_out, acc, st);
-    else launch_stage_p<P32R12>(stage, reunit, B, w_in, w_out, acc, st);
+template <int P, int STAGE, int MODE>
+static void launch_m(const Batch& B, const void* w_in, void* w_out, void* acc, void* clov, int reunit,
+                     cudaStream_t st) {
+    if (B.ncfg <= kSmallCap)
+        launch_cap<P, STAGE, MODE, kSmallCap>(B, w_in, w_out, acc, clov, reunit, st);
+    else
+        launch_cap<P, STAGE, MODE, kMaxCfg>(B, w_in, w_out, acc, clov, reunit, st);
+}
+
+template <int P>
+static void launch_stage_p(int stage, int mode, int reunit, const Batch& B, const void* w_in, void* w_out,
+                           void* acc, void* clov, cudaStream_t st) {
+    if (mode == 2) return launch_m<P, 1, 2>(B, w_in, w_out, acc, clov, reunit, st);
+    switch (stage) {
+        case 1:
+            if (mode == 1) launch_m<P, 1, 1>(B, w_in, w_out, acc, clov, reunit, st);
+            else launch_m<P, 1, 0>(B, w_in, w_out, acc, clov, reunit, st);
+            break;
+        case 2: launch_m<P, 2, 0>(B, w_in, w_out, acc, clov, reunit, st); break;
+        default: launch_m<P, 3, 0>(B, w_in, w_out, acc, clov, reunit, st); break;
+    }
+}
+
+void launch_stage(int prec, int stage, int mode, int reunit, const Batch& B, const void* w_in, void* w_out,
+                  void* acc, void* clov, cudaStream_t st) {
+    if (prec == P64) launch_stage_p<P64>(stage, mode, reunit, B, w_in, w_out, acc, clov, st);
+    else if (prec == P32) launch_stage_p<P32>(stage, mode, reunit, B, w_in, w_out, acc, clov, st);
+    else launch_stage_p<P32R12>(stage, mode, reunit, B, w_in, w_out, acc, clov, st);
 }
 
 }  // namespace tgf

@@ -79,7 +79,9 @@ def test_sizes(lib):
     assert lib.tgf_links_bytes(lib.TGF_FP32, lat) == sum(4 * 18 * 4 * v for v in Vp)
     assert lib.tgf_links_bytes(lib.TGF_FP32_R12, lat) == sum(4 * 12 * 4 * v for v in Vp)
     assert lib.tgf_accum_bytes(lib.TGF_FP64, lat) == sum(4 * 8 * 8 * v for v in Vp)
-    assert lib.tgf_scratch_bytes(lat) == sum((v + 127) // 128 for v in V) * 32
+    part = (sum((v + 127) // 128 for v in V) * 32 + 255) // 256 * 256
+    assert lib.tgf_scratch_bytes(lib.TGF_FP64, lat) == part + sum(114 * 8 * v for v in Vp)
+    assert lib.tgf_scratch_bytes(lib.TGF_FP32, lat) == part + sum(114 * 4 * v for v in Vp)
     assert lib.tgf_canonical_bytes(lib.lattices([(4, 4, 12, 12)])) == 2304 * 72 * 8
 
 
@@ -115,6 +117,7 @@ def test_flow_rejects_small_obs_capacity(lib):
     a = 1 << 20
     te = (C.c_double * 1)(0.18)
     nrec = (C.c_int * 1)()
-    s = lib._lib.tgf_flow(0, lat, 1, a, 2 * a, 3 * a, 4 * a, 1 << 20, 0.01, te, 1, 0, 0, 5 * a, 3, nrec, None)
+    sb = lib.tgf_scratch_bytes(0, lat)
+    s = lib._lib.tgf_flow(0, lat, 1, a, 2 * a, 3 * a, 4 * a, sb, 0.01, te, 1, 0, 0, 5 * a, 3, nrec, None)
     assert s == lib.TGF_EINVAL
     assert b"records" in lib._lib.tgf_last_error()
