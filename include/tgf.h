@@ -139,6 +139,24 @@ tgf_status tgf_measure(int prec, const tgf_lattice *lat, int ncfg, const void *l
                        double *scratch, size_t scratch_bytes, tgf_obs *obs_dev, size_t obs_stride,
                        int rec, double t, unsigned flags, void *stream);
 
+/* tgf_measure for callers that cannot allocate device memory: the same measurement, with the
+ * scratch held in a fixed device array inside the library instead of a caller buffer.  The
+ * paper has no counterpart; it serves code that may not call cudaMalloc, such as a plug-in
+ * whose host application owns all device memory and passes in only inputs and outputs, or a
+ * latency-critical loop that must avoid cudaMalloc's implicit device synchronisation.  The
+ * caller still passes the links and obs_dev (arguments as for tgf_measure).
+ * Limit: the array is 36 MiB (37748736 bytes) on every device that loads the library, held
+ * until the process exits; a batch whose tgf_scratch_bytes exceeds it is rejected with
+ * TGF_EINVAL and a message (about 41,000 sites in FP64, 82,000 in FP32 forms).
+ * Set-up: the first call on each device looks up the array's device address with
+ * cudaGetSymbolAddress (that device must be current); make that first call before any stream
+ * capture.  No call allocates or frees device memory.  All calls share the one array, which
+ * keeps the last call's contents; each call overwrites everything it reads, so nothing needs
+ * clearing, but calls whose kernels may overlap on the GPU (unordered streams) race. */
+tgf_status tgf_measure_noalloc(int prec, const tgf_lattice *lat, int ncfg, const void *links,
+                               tgf_obs *obs_dev, size_t obs_stride, int rec, double t,
+                               unsigned flags, void *stream);
+
 /* Flow every configuration c from t = 0 to t_end[c] (host array) in RK3 steps of eps: n_c =
  * floor(t_end[c]/eps) full steps, then one step of t_end[c] - n_c eps if that is > 1e-12 eps.
  * Observables are recorded into obs_dev[c * obs_cap + r] before every measure_every-th step

@@ -59,6 +59,7 @@ _SIGS = {
     "tgf_flow": [C.c_int, _LATP, C.c_int, _P, _P, _P, _P, _SZ, C.c_double, C.POINTER(C.c_double), C.c_int,
                  C.c_int, C.c_uint, _P, _SZ, C.POINTER(C.c_int), _P],
     "tgf_flow_records": [C.c_double, C.c_double, C.c_int, C.POINTER(C.c_int)],
+    "tgf_measure_noalloc": [C.c_int, _LATP, C.c_int, _P, _P, _SZ, C.c_int, C.c_double, C.c_uint, _P],
     "tgf_norm": [C.c_double, C.c_int, C.c_int, C.POINTER(C.c_double)],
     "tgf_fma_peak": [C.c_int, _P, C.c_int, C.c_int, C.POINTER(C.c_double), _P],
     "tgf_lambda": [C.c_double, C.c_int, C.c_double, C.POINTER(C.c_double), C.POINTER(C.c_double), C.c_int,
@@ -177,6 +178,12 @@ def tgf_measure(prec, lat, links, scratch, obs_dev, obs_stride, rec, t, flags=0,
     _check(_lib.tgf_measure(prec, lat, len(lat), _ptr(links), _ptr(scratch),
                             scratch.numel() * scratch.element_size(), _ptr(obs_dev), obs_stride, rec, t, flags,
                             _stream(stream)))
+
+
+def tgf_measure_noalloc(prec, lat, links, obs_dev, obs_stride, rec, t, flags=0, stream=None):
+    """tgf_measure with the library's fixed device scratch (no caller scratch, no allocation)."""
+    _check(_lib.tgf_measure_noalloc(prec, lat, len(lat), _ptr(links), _ptr(obs_dev), obs_stride, rec, t, flags,
+                                    _stream(stream)))
 
 
 def tgf_flow_records(eps, t_end, measure_every=1) -> int:

@@ -32,6 +32,20 @@ tgf_status fail(tgf_status st, const char* fmt, ...) {
     return st;
 }
 
+}  // namespace
+
+int tgf::set_error(int st, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return st;
+}
+
+namespace {
+
 #define TGF_CUDA(call)                                                                          \
     do {                                                                                        \
         cudaError_t e_ = (call);                                                                \

@@ -198,6 +198,9 @@ struct AccStore<float> {
 // host-side launchers (one translation unit each)
 // ---------------------------------------------------------------------------------------------
 
+// Record a failure message for tgf_last_error() and return `st` (host, printf-style).
+int set_error(int st, const char* fmt, ...);
+
 // mode: 0 = RK3 stage only; 1 = stage and clover halves of the input field; 2 = halves only
 void launch_stage(int prec, int stage, int mode, int reunit, const Batch& B, const void* w_in, void* w_out,
                   void* acc, void* clov, cudaStream_t st);

@@ -20,6 +20,9 @@ def tgf():
 
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
+    from paper_2107_03747_gb300 import build
+
+    build.build()
     from paper_2107_03747_gb300 import binding
 
     return binding
