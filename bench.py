@@ -170,12 +170,9 @@ def dist_init():
 def max_over_ranks(x, ws):
     if ws == 1:
         return x
-    import torch
-    import torch.distributed as dist
+    from paper_2107_03747_gb300 import replicas
 
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    return float(t.item())
+    return replicas.max_over_ranks(x)
 
 
 def barrier(ws):
@@ -388,6 +385,19 @@ def run_tgf(args):
         del b64
 
     clocks = clk.summary()
+    lam_all = {}
+    if ws > 1:
+        from paper_2107_03747_gb300 import replicas
+
+        o = torch.from_numpy(res_obs)
+        for key in sorted(set(lt)):
+            idx = [i for i in range(len(Ls)) if lt[i] == key]
+            E = [float(o[i, nrec[i] - 1, 1]) for i in idx]
+            Q = [float(o[i, nrec[i] - 1, 2]) for i in idx]
+            t = float(o[idx[0], nrec[idx[0]] - 1, 0])
+            lam_all[key] = replicas.ensemble_lambda(math.sqrt(8 * t) / key, key, t, E, Q)
+    else:
+        lam_all = lams
     if rank == 0:
         cpu = None
         if not args.no_cpu:
@@ -413,7 +423,7 @@ def run_tgf(args):
                     "d2h_bytes_per_step": obs_host.numel() * 8, "ms_per_step": ms_e2e},
             "gpu_launches": launches_per_flow(members) * args.steps,
             "roofline": roof, "cpu_baseline": cpu, "clocks": clocks,
-            "lambda_tgf": {str(k): v[0] for k, v in lams.items()},
+            "lambda_tgf": {str(k): {"lambda": v[0], "kept": v[1]} for k, v in lam_all.items()},
         }
         if acc:
             line["accuracy"] = acc
