@@ -299,3 +299,33 @@ def test_full_size_flow_properties_fp32(tgf):
     assert np.all(np.diff(o[:, 1]) < 0)
     g = b.get_links()[0]
     assert np.abs(g @ O.dag(g) - np.eye(3)).max() < 2e-6
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp32_r12"])
+def test_fp32_small_extents_and_twists_along_x3(tgf, prec):
+    """FP32 forms on extents 2 and odd extents along x3, with twists in planes that contain x3
+    (their twisted corners sit on the x3 = 0 and x3 = 1 slabs)."""
+    tw = np.zeros((4, 4), dtype=np.int64)
+    for a, b_, k in [(0, 1, 1), (0, 3, 1), (1, 3, 2), (2, 3, 1)]:
+        tw[a, b_], tw[b_, a] = k, -k
+    cases = [(2, 3, 4, 2), (3, 2, 2, 4), (4, 4, 4, 6), (3, 3, 5, 7)]
+    fields = [I.random_links(L, 70 + i, 0.5) for i, L in enumerate(cases)]
+    b = load(tgf, cases, fields, prec, [tgf.twist6(tw)] * len(cases))
+    g = b.measure()
+    for i, L in enumerate(cases):
+        o = O.measure(fields[i], tw)
+        assert g[i][1] == pytest.approx(o["E"], rel=2e-6)
+        assert abs(g[i][2] - o["Q"]) < 2e-5
+        assert g[i][3] == pytest.approx(o["P"], rel=2e-6)
+    for s in (1, 2, 3):
+        b.stage(s, 0.02)
+    got = b.get_links()
+    for i, L in enumerate(cases):
+        ref = O.rk3_step(fields[i], 0.02, tw)
+        assert np.abs(got[i] - ref).max() < 5e-6, (L, np.abs(got[i] - ref).max())
+    obs, n = b.flow(0.02, 0.06)
+    o = obs.cpu().numpy()
+    for i, L in enumerate(cases):
+        _, rec = O.flow(O.rk3_step(fields[i], 0.02, tw), 0.02, 0.06, tw)
+        for gg, r in zip(o[i, : n[i]], rec):
+            assert gg[1] == pytest.approx(r[1], rel=5e-6)
