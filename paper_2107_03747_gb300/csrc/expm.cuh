@@ -28,8 +28,10 @@ struct series_tol<float> {
     static constexpr float v = 1e-9f;
 };
 
-// exp(X) for X given by its 8 parameters (see alg8).
-template <class T>
+// exp(X) for X given by its 8 parameters (see alg8); with MINUS_ONE, exp(X) - 1 with the unit
+// matrix taken out of the series (f0 - 1 summed from its second term), so that small X keep
+// their full relative precision.
+template <class T, bool MINUS_ONE = false>
 __device__ __forceinline__ void expm_su3(mat3<T>& m, const alg8<T>& x) {
     // Q = -i X
     const T q00 = x.v[0], q11 = x.v[1], q22 = -(x.v[0] + x.v[1]);
@@ -62,7 +64,9 @@ __device__ __forceinline__ void expm_su3(mat3<T>& m, const alg8<T>& x) {
     // f_j = sum_n i^n (alpha_n, beta_n, gamma_n) / n!, summed four terms at a time
     // (i^n cycles i, -1, -i, +1 within a block; at most 20 terms, ||Q||_F <= 1 here)
     T a = T(1), b = T(0), g = T(0);
-    T f0r = T(1), f0i = T(0), f1r = T(0), f1i = T(0), f2r = T(0), f2i = T(0);
+    // f0 starts at 1 (the n = 0 term) unless the unit matrix is taken out; with scaling and
+    // squaring the full matrix is needed first and 1 is subtracted at the end
+    T f0r = (MINUS_ONE && s == 0) ? T(0) : T(1), f0i = T(0), f1r = T(0), f1i = T(0), f2r = T(0), f2i = T(0);
     const T tol = series_tol<T>::v;
 #pragma unroll
     for (int blk = 0; blk < 5; ++blk) {
@@ -116,6 +120,11 @@ __device__ __forceinline__ void expm_su3(mat3<T>& m, const alg8<T>& x) {
     for (int k = 0; k < s; ++k) {
         mat3<T> t = m;
         mul_nn(m, t, t);
+    }
+    if (MINUS_ONE && s > 0) {
+        m.e[0][0].re -= T(1);
+        m.e[1][1].re -= T(1);
+        m.e[2][2].re -= T(1);
     }
 }
 

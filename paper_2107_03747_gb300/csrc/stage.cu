@@ -63,6 +63,7 @@ constexpr int stage_min_blocks() { return P == P64 ? 2 : TGF_STAGE_MINB32; }
 // Plane index of (mu, nu), mu < nu, in the order 01, 23, 02, 13, 03, 12 (consecutive planes
 // pair up in the topological charge); -1 for mu >= nu.
 __constant__ int8_t c_plane_of[4][4] = {{-1, 0, 2, 4}, {-1, -1, 5, 3}, {-1, -1, -1, 1}, {-1, -1, -1, -1}};
+__constant__ int8_t c_pair[6][2] = {{0, 1}, {2, 3}, {0, 2}, {1, 3}, {0, 3}, {1, 2}};
 
 // The anti-Hermitian part D - D^+ of a 3x3 matrix as 9 reals (2 Im D_jj; D_jk - conj(D_kj), j<k),
 // written to 9 component planes of length Vp.
@@ -96,24 +97,43 @@ k_stage(const __grid_constant__ BatchT<CAP> B, const typename Store<P>::T* __res
     using T = typename Store<P>::T;
     using S = Store<P>;
     constexpr int R = S::reals;
-    constexpr int WPD = SPB / 32;  // warps per direction
+    static_assert(SPB == 32, "one warp per direction: the block's four warps share 32 sites");
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int mu = warp / WPD;
-    if (MODE == 2 && mu == 3) return;  // no plane (3, nu) with nu > 3
+    const int mu = warp;
+    // T_{ab}(n) = U_b(n+a) U_a(n+b)^+ of the six planes a < b: the forward staple of link (n, a) in
+    // direction b is T_ab U_b(n)^+, that of link (n, b) in direction a is T_ab^+ U_a(n)^+, so in
+    // FP64 (bound by the FP64 pipe) each is computed once per site by one warp of the block and
+    // shared (42 instead of 48 staple products per site).  The FP32 forms are bound by instruction
+    // issue and latency, where the barrier costs more than the saved products: they recompute.
+    constexpr bool SHARE = (P == P64);
+    __shared__ cx<T> sT[SHARE ? 6 : 1][9][32];
 
     for (int blk = blockIdx.x; blk < B.nblk; blk += gridDim.x) {
         const int ci = find_cfg(B, blk);
         const CfgDesc& c = B.c[ci];
-        const int s = (blk - c.blk0) * SPB + (warp % WPD) * 32 + lane;
-        if (s >= c.V) continue;
-        const uint64_t xp = pack_coords(c, s);
+        const int s = (blk - c.blk0) * SPB + lane;
+        const bool valid = s < c.V;
+        const uint64_t xp = valid ? pack_coords(c, s) : 0;
         const int Vp = c.Vp;
         const T* base = w_in + c.w_off;
         auto link = [&](int dir, int site, mat3<T>& u) { S::load(base + (size_t)dir * R * Vp, Vp, site, u); };
+        mat3<T> sig, a, b, t;
+        if constexpr (SHARE) {
+            // phase 1: warp w builds T of planes w and w + 4 (pair order 01, 23, 02, 13, 03, 12)
+            for (int pr = warp; pr < 6; pr += 4) {
+                if (!valid) break;
+                const int pa = c_pair[pr][0], pb = c_pair[pr][1];
+                link(pb, step_p(s, coord(xp, pa), c.L[pa], c.st[pa]), a);
+                link(pa, step_p(s, coord(xp, pb), c.L[pb], c.st[pb]), b);
+                mul_nd(t, a, b);
+#pragma unroll
+                for (int k = 0; k < 9; ++k) sT[pr][k][lane] = t.e[k / 3][k % 3];
+            }
+            __syncthreads();
+        }
+        auto link_body = [&]() {
         const int xm = coord(xp, mu), Lm = c.L[mu], Sm = c.st[mu];
         const int s_mp = step_p(s, xm, Lm, Sm);
-
-        mat3<T> sig, a, b, t;
         if (MODE != 2) set_zero(sig);
 #pragma unroll 1
         for (int dn = 1; dn < 4; ++dn) {
@@ -121,25 +141,42 @@ k_stage(const __grid_constant__ BatchT<CAP> B, const typename Store<P>::T* __res
             const bool clover = MODE != 0 && nu > mu;
             if (MODE == 2 && !clover) continue;
             const int xn = coord(xp, nu), Ln = c.L[nu], Sn = c.st[nu];
-            const int s_np = step_p(s, xn, Ln, Sn);
             const int s_nm = step_m(s, xn, Ln, Sn);
             const int s_mp_nm = step_p(s_nm, xm, Lm, Sm);
             const int k = c.tw[mu * 4 + nu];
             T zr = T(1), zi = T(0);
             if (k != 0) centre<T>(k, zr, zi);
-            // forward staple F = Z*_{mu nu}(n) U_nu(n+mu) U_mu(n+nu)^+ U_nu(n)^+
-            link(nu, s_mp, a);
-            link(mu, s_np, b);
-            mul_nd(t, a, b);
-            link(nu, s, a);
+            // forward staple F = Z*_{mu nu}(n) U_nu(n+mu) U_mu(n+nu)^+ U_nu(n)^+ = Z* T_{mu nu} U_nu(n)^+
             const bool tw_f = k != 0 && xm == 0 && xn == 0;
             mat3<T> f;
-            if (clover || tw_f) {
-                mul_nd(f, t, a);
-                if (tw_f) scale_cx(f, zr, -zi);
-                if (MODE != 2) add_to(sig, f);
+            if constexpr (SHARE) {
+                // T_{mu nu} = T_{nu mu}^+ from the block's shared T of the plane
+                const int pl_f = c_plane_of[mu < nu ? mu : nu][mu < nu ? nu : mu];
+#pragma unroll
+                for (int kk = 0; kk < 9; ++kk) t.e[kk / 3][kk % 3] = sT[pl_f][kk][lane];
             } else {
-                mul_nd_acc(sig, t, a);
+                link(nu, step_p(s, xm, Lm, Sm), a);
+                link(mu, step_p(s, xn, Ln, Sn), b);
+                mul_nd(t, a, b);
+            }
+            link(nu, s, a);
+            if (!SHARE || nu > mu) {
+                if (clover || tw_f) {
+                    mul_nd(f, t, a);
+                    if (tw_f) scale_cx(f, zr, -zi);
+                    if (MODE != 2) add_to(sig, f);
+                } else {
+                    mul_nd_acc(sig, t, a);
+                }
+            } else {
+                // F = T_{nu mu}^+ U_nu(n)^+ = (U_nu(n) T_{nu mu})^+
+                mul_nn(b, a, t);
+#pragma unroll
+                for (int i = 0; i < 3; ++i)
+#pragma unroll
+                    for (int j = 0; j < 3; ++j) f.e[i][j] = {b.e[j][i].re, -b.e[j][i].im};
+                if (tw_f) scale_cx(f, zr, -zi);
+                add_to(sig, f);
             }
             // backward staple B = Z_{mu nu}(n-nu) U_nu(n+mu-nu)^+ U_mu(n-nu)^+ U_nu(n-nu)
             link(mu, s_nm, a);
@@ -180,7 +217,7 @@ k_stage(const __grid_constant__ BatchT<CAP> B, const typename Store<P>::T* __res
                 store_ah(cb + (size_t)(pl * 2 + 1) * 9 * Vp, Vp, s_mp, t);
             }
         }
-        if (MODE == 2) continue;
+        if (MODE == 2) return;
         // Omega = U_mu(n) Sigma, Z = -P_ta(Omega)
         mat3<T> u;
         link(mu, s, u);
@@ -205,10 +242,16 @@ k_stage(const __grid_constant__ BatchT<CAP> B, const typename Store<P>::T* __res
 #pragma unroll
             for (int i = 0; i < 8; ++i) x.v[i] = T(0.75) * h * z.v[i] - x.v[i];
         }
-        expm_su3(b, x);
+        // W' = W + (exp(X) - 1) W: the update rounds once on top of W instead of through a full
+        // product, which keeps the FP32 forms' drift off SU(3) small between re-projections
+        expm_su3<T, true>(b, x);
         mul_nn(t, b, u);
+        add_to(t, u);
         if (STAGE == 3 && P != P64 && reunit) reunitarize(t);
         S::store(w_out + c.w_off + (size_t)mu * R * Vp, Vp, s, t);
+        };
+        if (valid) link_body();
+        if constexpr (SHARE) __syncthreads();  // sT is rewritten by the next block of the grid-stride loop
     }
 }
 
