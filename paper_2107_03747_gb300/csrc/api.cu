@@ -222,6 +222,31 @@ std::list<GraphEntry> g_graphs;  // most recent first
 constexpr size_t kGraphCache = 8;
 cudaStream_t g_capture[64] = {};
 
+// Side branch of a flow: the clover sum + reduction of a measured step (HBM-bound) runs on this
+// stream while stages 2 and 3 (FP-pipe-bound) run on the main one; captured into the same graph
+// as parallel nodes.
+struct SideBranch {
+    cudaStream_t s = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
+};
+SideBranch g_side[64];
+std::mutex g_side_mu;
+
+tgf_status side_branch(SideBranch*& out) {
+    int dev = 0;
+    TGF_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return fail(TGF_EINVAL, "device %d out of range", dev);
+    std::lock_guard<std::mutex> lk(g_side_mu);
+    SideBranch& sb = g_side[dev];
+    if (!sb.s) {
+        TGF_CUDA(cudaStreamCreateWithFlags(&sb.s, cudaStreamNonBlocking));
+        TGF_CUDA(cudaEventCreateWithFlags(&sb.fork, cudaEventDisableTiming));
+        TGF_CUDA(cudaEventCreateWithFlags(&sb.join, cudaEventDisableTiming));
+    }
+    out = &sb;
+    return TGF_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -408,6 +433,16 @@ static tgf_status enqueue_flow(int prec, const tgf_lattice* lat, int ncfg, const
     std::vector<int> rec(ncfg, 0);
     void* cur = w;
     void* alt = w_tmp;
+    SideBranch* sb = nullptr;
+    if ((s = side_branch(sb))) return s;
+    bool pending = false;  // a side-branch sum still reads the clover halves / writes the partials
+    auto join = [&]() -> tgf_status {
+        if (pending) {
+            TGF_CUDA(cudaStreamWaitEvent(st, sb->join, 0));
+            pending = false;
+        }
+        return TGF_OK;
+    };
     // configurations with nothing to integrate: one record at t = 0
     {
         std::vector<int> which, r;
@@ -434,9 +469,16 @@ static tgf_status enqueue_flow(int prec, const tgf_lattice* lat, int ncfg, const
             B.c[k].h = (i < n[c]) ? eps : rest[c];
         }
         const int ru = (prec != TGF_FP64 && reunit_every > 0 && (i + 1) % reunit_every == 0) ? 1 : 0;
+        if (mode1 && (s = join())) return s;  // stage 1 is about to rewrite the halves
         launch_stage(prec, 1, mode1, 0, B, cur, alt, accum, clover_base(scratch, Ly), st);
         if ((s = last_launch("stage 1"))) return s;
-        if (mode1 && (s = enqueue_sum(prec, flags, lat, Ly, mw, mr, mt, obs_cap, scratch, obs, st))) return s;
+        if (mode1) {
+            TGF_CUDA(cudaEventRecord(sb->fork, st));
+            TGF_CUDA(cudaStreamWaitEvent(sb->s, sb->fork, 0));
+            if ((s = enqueue_sum(prec, flags, lat, Ly, mw, mr, mt, obs_cap, scratch, obs, sb->s))) return s;
+            TGF_CUDA(cudaEventRecord(sb->join, sb->s));
+            pending = true;
+        }
         launch_stage(prec, 2, 0, 0, B, alt, cur, accum, nullptr, st);
         if ((s = last_launch("stage 2"))) return s;
         launch_stage(prec, 3, 0, ru, B, cur, alt, accum, nullptr, st);
@@ -446,9 +488,12 @@ static tgf_status enqueue_flow(int prec, const tgf_lattice* lat, int ncfg, const
         std::vector<double> ft;
         for (int c : act)
             if (total[c] == i + 1) { fw.push_back(c); fr.push_back(rec[c]++); ft.push_back((double)n[c] * eps + rest[c]); }
-        if (!fw.empty() && (s = enqueue_measure(prec, flags, lat, Ly, fw, fr, ft, obs_cap, cur, scratch, obs, st)))
-            return s;
+        if (!fw.empty()) {
+            if ((s = join())) return s;
+            if ((s = enqueue_measure(prec, flags, lat, Ly, fw, fr, ft, obs_cap, cur, scratch, obs, st))) return s;
+        }
     }
+    if ((s = join())) return s;
     // configurations that finished after an odd number of steps hold their field in w_tmp
     const size_t rs = real_size(prec);
     for (int c = 0; c < ncfg; ++c) {
