@@ -157,6 +157,16 @@ tgf_status tgf_measure_noalloc(int prec, const tgf_lattice *lat, int ncfg, const
                                tgf_obs *obs_dev, size_t obs_stride, int rec, double t,
                                unsigned flags, void *stream);
 
+/* Time-slice topological charge q(x0, t) (Sec. 4): the clover charge density (eq. qlatt) summed
+ * over the three directions other than `dir` at each slab x_dir = x, for every configuration at
+ * the current field; q_dev[c * q_stride + x] for x = 0..L[dir]-1 (q_stride >= every L[dir]).
+ * For the TGF box `dir` is a long direction (2 or 3), so the sum runs over both short ones.
+ * FP64 sums in a fixed order; the slices of a configuration add up to its Q.  Uses the same
+ * scratch as tgf_measure. */
+tgf_status tgf_measure_slices(int prec, const tgf_lattice *lat, int ncfg, const void *links,
+                              double *scratch, size_t scratch_bytes, int dir, double *q_dev,
+                              size_t q_stride, unsigned flags, void *stream);
+
 /* Flow every configuration c from t = 0 to t_end[c] (host array) in RK3 steps of eps: n_c =
  * floor(t_end[c]/eps) full steps, then one step of t_end[c] - n_c eps if that is > 1e-12 eps.
  * Observables are recorded into obs_dev[c * obs_cap + r] before every measure_every-th step
@@ -184,6 +194,13 @@ tgf_status tgf_norm(double c, int Ltilde, int N, double *norm_out);
  * Returns TGF_ESTATE (and n_kept = 0) when no configuration passes the cut. */
 tgf_status tgf_lambda(double c, int Ltilde, double t, const double *E, const double *Q, int ncfg,
                       double *lambda_out, int *n_kept);
+
+/* Correlator of the time-slice charge in the zero-charge sector (eq. qcorr), host only:
+ * C[d] = sum_c delta_c (1/T) sum_x q_c(x + d) q_c(x) / sum_c delta_c, d = 0..T-1 (periodic),
+ * delta_c = [|Q_c| < 1/2]; q is [ncfg][q_stride] (T <= q_stride).  TGF_ESTATE when no
+ * configuration is kept. */
+tgf_status tgf_slice_correlator(const double *q, size_t q_stride, const double *Q, int ncfg, int T,
+                                double *C_out, int *n_kept);
 
 /* ---- diagnostics ---------------------------------------------------------------------------- */
 

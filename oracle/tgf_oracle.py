@@ -335,6 +335,47 @@ def measure(U: np.ndarray, twist, traceless: bool = False, corner=(0, 0, 0, 0)) 
     }
 
 
+def charge_density(U: np.ndarray, twist, traceless: bool = False, corner=(0, 0, 0, 0)) -> np.ndarray:
+    """q(n) = 1/(16 pi^2) Tr[G_{mu nu}(n) Gt_{mu nu}(n)] per site (the summand of eq. qlatt), shape (L3, L2, L1, L0)."""
+    G = field_strength(U, twist, traceless, corner)
+    q = 0.0
+    for mu in range(4):
+        for nu in range(4):
+            if mu == nu:
+                continue
+            for rho in range(4):
+                for sig in range(4):
+                    eps = levi_civita(mu, nu, rho, sig)
+                    if eps:
+                        q = q + 0.5 * eps * tr(mm(G[mu][nu], G[rho][sig]))
+    return np.real(q) / (16.0 * math.pi ** 2)
+
+
+def slice_charge(U: np.ndarray, twist, direction: int = 3, traceless: bool = False, corner=(0, 0, 0, 0)) -> np.ndarray:
+    """q(x0, t) of Sec. 4: the charge density summed over the three directions other than
+    `direction` (a long one, so the sum includes both short directions); entry x is the slice
+    x_direction = x (lattice units)."""
+    q = charge_density(U, twist, traceless, corner)
+    axes = tuple(a for a in range(4) if a != _axis(direction))
+    return np.sum(q, axis=axes)
+
+
+def slice_correlator(q_slices, Q, keep_cut: float = 0.5):
+    """C(d) = <q(x0 + d) q(x0) delta_Q> / <delta_Q> (eq. qcorr) for an ensemble, averaged over the
+    source x0 (translation invariance); q_slices[c][x], Q[c] per configuration.
+    Returns (C as an array over d = 0..T-1, number of configurations kept) or (None, 0)."""
+    q = np.asarray(q_slices, dtype=np.float64)
+    keep = np.abs(np.asarray(Q, dtype=np.float64)) < keep_cut
+    if not np.any(keep):
+        return None, 0
+    T = q.shape[1]
+    C = np.zeros(T)
+    for c in np.nonzero(keep)[0]:
+        for d in range(T):
+            C[d] += np.mean(np.roll(q[c], -d) * q[c])
+    return C / np.sum(keep), int(np.sum(keep))
+
+
 def flow(U: np.ndarray, eps: float, t_end: float, twist, measure_every: int = 1,
          traceless: bool = False, corner=(0, 0, 0, 0)):
     """Integrate the flow from t = 0 to t_end with RK3 steps of size eps.

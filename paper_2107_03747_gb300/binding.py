@@ -59,6 +59,9 @@ _SIGS = {
     "tgf_flow": [C.c_int, _LATP, C.c_int, _P, _P, _P, _P, _SZ, C.c_double, C.POINTER(C.c_double), C.c_int,
                  C.c_int, C.c_uint, _P, _SZ, C.POINTER(C.c_int), _P],
     "tgf_flow_records": [C.c_double, C.c_double, C.c_int, C.POINTER(C.c_int)],
+    "tgf_measure_slices": [C.c_int, _LATP, C.c_int, _P, _P, _SZ, C.c_int, _P, _SZ, C.c_uint, _P],
+    "tgf_slice_correlator": [C.POINTER(C.c_double), _SZ, C.POINTER(C.c_double), C.c_int, C.c_int,
+                             C.POINTER(C.c_double), C.POINTER(C.c_int)],
     "tgf_measure_noalloc": [C.c_int, _LATP, C.c_int, _P, _P, _SZ, C.c_int, C.c_double, C.c_uint, _P],
     "tgf_norm": [C.c_double, C.c_int, C.c_int, C.POINTER(C.c_double)],
     "tgf_fma_peak": [C.c_int, _P, C.c_int, C.c_int, C.POINTER(C.c_double), _P],
@@ -186,6 +189,27 @@ def tgf_measure_noalloc(prec, lat, links, obs_dev, obs_stride, rec, t, flags=0, 
                                     _stream(stream)))
 
 
+def tgf_measure_slices(prec, lat, links, scratch, dir, q_dev, q_stride, flags=0, stream=None):
+    _check(_lib.tgf_measure_slices(prec, lat, len(lat), _ptr(links), _ptr(scratch),
+                                   scratch.numel() * scratch.element_size(), dir, _ptr(q_dev), q_stride, flags,
+                                   _stream(stream)))
+
+
+def tgf_slice_correlator(q, Q):
+    """q: (ncfg, T) array of slice charges, Q: (ncfg,) charges -> (C over d = 0..T-1, kept) or (None, 0)."""
+    q = np.ascontiguousarray(np.asarray(q, dtype=np.float64))
+    Qa = np.ascontiguousarray(np.asarray(Q, dtype=np.float64))
+    n, T = q.shape
+    out = np.zeros(T)
+    kept = C.c_int()
+    s = _lib.tgf_slice_correlator(q.ctypes.data_as(C.POINTER(C.c_double)), T, Qa.ctypes.data_as(C.POINTER(C.c_double)),
+                                  n, T, out.ctypes.data_as(C.POINTER(C.c_double)), C.byref(kept))
+    if s == TGF_ESTATE:
+        return None, 0
+    _check(s)
+    return out, kept.value
+
+
 def tgf_flow_records(eps, t_end, measure_every=1) -> int:
     out = C.c_int()
     _check(_lib.tgf_flow_records(eps, t_end, measure_every, C.byref(out)))
@@ -300,6 +324,16 @@ class FlowBatch:
         obs = torch.zeros(self.ncfg * 5, dtype=torch.float64, device=self.device)
         tgf_measure(self.prec, self.lat, self.links, self.scratch, obs, 1, 0, t, flags, stream)
         return obs.cpu().numpy().reshape(self.ncfg, 5)
+
+    def slices(self, direction=3, flags=0, stream=None):
+        """q(x, t) per configuration along `direction` as a list of numpy arrays."""
+        import torch
+
+        T = max(L[direction] for L in self.Ls)
+        q = torch.zeros(self.ncfg * T, dtype=torch.float64, device=self.device)
+        tgf_measure_slices(self.prec, self.lat, self.links, self.scratch, direction, q, T, flags, stream)
+        qn = q.cpu().numpy().reshape(self.ncfg, T)
+        return [qn[c, : L[direction]].copy() for c, L in enumerate(self.Ls)]
 
     def stage(self, stage, eps, reunit=0, stream=None):
         """One RK3 stage from ``links`` into ``links_tmp``; then the two are swapped."""

@@ -406,6 +406,38 @@ tgf_status tgf_measure(int prec, const tgf_lattice* lat, int ncfg, const void* l
                            (cudaStream_t)stream);
 }
 
+tgf_status tgf_measure_slices(int prec, const tgf_lattice* lat, int ncfg, const void* links, double* scratch,
+                              size_t scratch_bytes, int dir, double* q_dev, size_t q_stride, unsigned flags,
+                              void* stream) {
+    tgf_status s;
+    if ((s = check_prec(prec)) || (s = check_lat(lat, ncfg)) || (s = check_ptr(links, "links")) ||
+        (s = check_ptr(scratch, "scratch")) || (s = check_ptr(q_dev, "q_dev")))
+        return s;
+    if (dir < 0 || dir > 3) return fail(TGF_EINVAL, "direction %d outside 0..3", dir);
+    Layout Ly = layout(prec, lat, ncfg);
+    if (scratch_bytes < Ly.scratch_bytes(prec))
+        return fail(TGF_EINVAL, "scratch of %zu bytes too small (need %zu)", scratch_bytes, Ly.scratch_bytes(prec));
+    for (int c = 0; c < ncfg; ++c)
+        if ((size_t)lat[c].L[dir] > q_stride)
+            return fail(TGF_EINVAL, "q_stride %zu < extent %d of configuration %d", q_stride, lat[c].L[dir], c);
+    cudaStream_t st = (cudaStream_t)stream;
+    std::vector<int> which = all_cfgs(ncfg);
+    Batch H = make_batch(lat, Ly, which, 32);
+    launch_stage(prec, 1, 2, 0, H, links, nullptr, nullptr, clover_base(scratch, Ly), st);
+    if ((s = last_launch("clover halves"))) return s;
+    // one block per (configuration, slab)
+    Batch Q = make_batch(lat, Ly, which, 1);
+    int blk = 0;
+    for (int c = 0; c < ncfg; ++c) {
+        Q.c[c].blk0 = blk;
+        Q.c[c].rec = c;
+        blk += lat[c].L[dir];
+    }
+    Q.nblk = blk;
+    launch_slice_charge(prec, flags, Q, clover_base(scratch, Ly), dir, q_dev, (int)q_stride, st);
+    return last_launch("slice charge");
+}
+
 tgf_status tgf_flow_records(double eps, double t_end, int measure_every, int* n_records) {
     if (!(eps > 0) || !std::isfinite(eps)) return fail(TGF_EINVAL, "eps = %g must be positive", eps);
     if (!(t_end >= 0) || !std::isfinite(t_end)) return fail(TGF_EINVAL, "t_end = %g must be >= 0", t_end);

@@ -91,3 +91,25 @@ extern "C" tgf_status tgf_lambda(double c, int Lt, double t, const double* E, co
     *lambda_out = norm * t * t * num / (3.0 * kept);
     return TGF_OK;
 }
+
+extern "C" tgf_status tgf_slice_correlator(const double* q, size_t q_stride, const double* Q, int ncfg, int T,
+                                           double* C_out, int* n_kept) {
+    if (!q || !Q || !C_out || !n_kept || ncfg < 1 || T < 1 || (size_t)T > q_stride) return TGF_EINVAL;
+    // C(d) = <q(x0 + d) q(x0) delta_Q> / <delta_Q>, averaged over the source x0 (eq. qcorr)
+    for (int d = 0; d < T; ++d) C_out[d] = 0.0;
+    int kept = 0;
+    for (int c = 0; c < ncfg; ++c) {
+        if (!(std::fabs(Q[c]) < 0.5)) continue;
+        ++kept;
+        const double* qc = q + (size_t)c * q_stride;
+        for (int d = 0; d < T; ++d) {
+            double acc = 0.0;
+            for (int x = 0; x < T; ++x) acc += qc[(x + d) % T] * qc[x];
+            C_out[d] += acc / T;
+        }
+    }
+    *n_kept = kept;
+    if (kept == 0) return TGF_ESTATE;
+    for (int d = 0; d < T; ++d) C_out[d] /= kept;
+    return TGF_OK;
+}

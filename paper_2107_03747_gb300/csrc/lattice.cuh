@@ -207,6 +207,9 @@ void launch_stage(int prec, int stage, int mode, int reunit, const Batch& B, con
 void launch_clover_sum(int prec, unsigned flags, const Batch& B, const void* clov, double* partial,
                        cudaStream_t st);
 void launch_reduce(const Batch& B, const double* partial, double* obs, cudaStream_t st);
+// per-slab sums of the charge density along `dir`; the batch has L[dir] blocks per configuration
+void launch_slice_charge(int prec, unsigned flags, const Batch& B, const void* clov, int dir, double* q, int q_stride,
+                         cudaStream_t st);
 void launch_pack(int prec, const Batch& B, const double* canon, void* w, cudaStream_t st);
 void launch_unpack(int prec, const Batch& B, const void* w, double* canon, cudaStream_t st);
 

@@ -130,6 +130,89 @@ k_reduce(const __grid_constant__ BatchT<CAP> B, const double* __restrict__ parti
     }
 }
 
+// q(x0, t) (Sec. 4): the charge density summed over the slab x_dir = x of each configuration,
+// one block per (configuration, slab), FP64 sums in a fixed order.  The launch descriptor has
+// L[dir] blocks per configuration; q_out[cfg_index * q_stride + x] with cfg_index = c.rec.
+template <class T, int CAP>
+__global__ void __launch_bounds__(256)
+k_slice_charge(const __grid_constant__ BatchT<CAP> B, const T* __restrict__ clov, int dir, double* __restrict__ q_out,
+               int q_stride, int traceless) {
+    __shared__ double red[256];
+    for (int blk = blockIdx.x; blk < B.nblk; blk += gridDim.x) {
+        const int ci = find_cfg(B, blk);
+        const CfgDesc& c = B.c[ci];
+        const int x = blk - c.blk0;
+        const int n_slab = c.V / c.L[dir];
+        const T* cb = clov + c.m_off;
+        const size_t Vp = (size_t)c.Vp;
+        double acc = 0.0;
+        for (int j = threadIdx.x; j < n_slab; j += 256) {
+            int r = j, s = x * c.st[dir];
+#pragma unroll
+            for (int d = 0; d < 4; ++d) {
+                if (d == dir) continue;
+                s += (r % c.L[d]) * c.st[d];
+                r /= c.L[d];
+            }
+            T a0[9], tq = T(0);
+#pragma unroll
+            for (int p = 0; p < 6; ++p) {
+                T a[9];
+#pragma unroll
+                for (int k = 0; k < 9; ++k)
+                    a[k] = __ldg(cb + (size_t)((p * 2) * 9 + k) * Vp + s) + __ldg(cb + (size_t)((p * 2 + 1) * 9 + k) * Vp + s);
+                if (traceless) {
+                    const T tr = (a[0] + a[1] + a[2]) * (T(1) / T(3));
+                    a[0] -= tr; a[1] -= tr; a[2] -= tr;
+                }
+                if (p & 1) {
+                    const T d = a0[0] * a[0] + a0[1] * a[1] + a0[2] * a[2] +
+                                T(2) * (a0[3] * a[3] + a0[4] * a[4] + a0[5] * a[5] + a0[6] * a[6] + a0[7] * a[7] + a0[8] * a[8]);
+                    tq += (p == 3) ? -d : d;
+                } else {
+#pragma unroll
+                    for (int k = 0; k < 9; ++k) a0[k] = a[k];
+                }
+            }
+            acc += (double)tq;
+        }
+        red[threadIdx.x] = acc;
+        __syncthreads();
+        for (int w = 128; w > 0; w >>= 1) {
+            if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) {
+            const double pi = 3.14159265358979323846;
+            q_out[(size_t)c.rec * q_stride + x] = red[0] / (256.0 * pi * pi);
+        }
+        __syncthreads();
+    }
+}
+
+template <class T, int CAP>
+static void slices_cap(const Batch& B, const void* clov, int dir, double* q, int q_stride, unsigned flags,
+                       cudaStream_t st) {
+    if constexpr (CAP == kMaxCfg) {
+        k_slice_charge<T, kMaxCfg><<<B.nblk, 256, 0, st>>>(B, (const T*)clov, dir, q, q_stride, (int)(flags & 1u));
+    } else {
+        BatchT<CAP> b;
+        b.ncfg = B.ncfg;
+        b.nblk = B.nblk;
+        for (int i = 0; i < B.ncfg; ++i) b.c[i] = B.c[i];
+        k_slice_charge<T, CAP><<<B.nblk, 256, 0, st>>>(b, (const T*)clov, dir, q, q_stride, (int)(flags & 1u));
+    }
+}
+
+void launch_slice_charge(int prec, unsigned flags, const Batch& B, const void* clov, int dir, double* q, int q_stride,
+                         cudaStream_t st) {
+    const bool small = B.ncfg <= kSmallCap;
+    if (prec == P64) small ? slices_cap<double, kSmallCap>(B, clov, dir, q, q_stride, flags, st)
+                           : slices_cap<double, kMaxCfg>(B, clov, dir, q, q_stride, flags, st);
+    else small ? slices_cap<float, kSmallCap>(B, clov, dir, q, q_stride, flags, st)
+               : slices_cap<float, kMaxCfg>(B, clov, dir, q, q_stride, flags, st);
+}
+
 template <class T, int CAP>
 static void sum_cap(unsigned flags, const Batch& B, const void* clov, double* partial, cudaStream_t st) {
     if constexpr (CAP == kMaxCfg) {

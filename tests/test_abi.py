@@ -121,3 +121,17 @@ def test_flow_rejects_small_obs_capacity(lib):
     s = lib._lib.tgf_flow(0, lat, 1, a, 2 * a, 3 * a, 4 * a, sb, 0.01, te, 1, 0, 0, 5 * a, 3, nrec, None)
     assert s == lib.TGF_EINVAL
     assert b"records" in lib._lib.tgf_last_error()
+
+
+def test_slice_correlator_matches_oracle(lib):
+    from oracle import tgf_oracle as O
+
+    rng = np.random.default_rng(4)
+    q = rng.normal(size=(6, 9)) * 0.08
+    Q = q.sum(axis=1)
+    Q[2] = 0.7  # cut by |Q| < 1/2
+    C, kept = lib.tgf_slice_correlator(q, Q)
+    Co, ko = O.slice_correlator(q, Q)
+    assert kept == ko
+    assert np.allclose(C, Co, rtol=1e-13, atol=1e-16)
+    assert lib.tgf_slice_correlator(q, [0.9] * 6) == (None, 0)

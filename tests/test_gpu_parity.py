@@ -329,3 +329,33 @@ def test_fp32_small_extents_and_twists_along_x3(tgf, prec):
         _, rec = O.flow(O.rk3_step(fields[i], 0.02, tw), 0.02, 0.06, tw)
         for gg, r in zip(o[i, : n[i]], rec):
             assert gg[1] == pytest.approx(r[1], rel=5e-6)
+
+
+# ---- time-slice charge (Sec. 4) --------------------------------------------------------------------
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("fp32", 2e-6)])
+def test_slice_charge_matches_oracle(tgf, prec, tol):
+    Ls = [(4, 4, 12, 12), (3, 3, 5, 7)]
+    fields = [I.random_links(L, 80 + i, 0.6) for i, L in enumerate(Ls)]
+    b = load(tgf, Ls, fields, prec)
+    for direction in (3, 2, 0):
+        got = b.slices(direction)
+        for U, g in zip(fields, got):
+            ref = O.slice_charge(U, TW, direction)
+            scale = max(1.0, np.abs(ref).max())
+            assert np.abs(g - ref).max() <= tol * scale, (direction, np.abs(g - ref).max())
+    # slices add up to Q
+    g = b.measure()
+    for i, q in enumerate(b.slices(3)):
+        assert q.sum() == pytest.approx(g[i][2], abs=tol * 10)
+
+
+def test_slice_charge_full_size_l16_sums_to_q(tgf):
+    L = (16, 16, 48, 48)
+    U = I.random_links(L, 2, 0.4)
+    b = load(tgf, [L], [U], "fp32")
+    b.flow(0.01, 0.3)
+    q = b.slices(3)[0]
+    Q = b.measure()[0][2]
+    assert q.shape == (48,)
+    assert q.sum() == pytest.approx(Q, abs=1e-5)

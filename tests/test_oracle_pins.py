@@ -229,3 +229,45 @@ def test_flow_records_and_partial_final_step():
     assert np.abs(Uf - U2).max() == 0.0
     Ef = [r[1] for r in rec]
     assert all(x > y for x, y in zip(Ef, Ef[1:]))
+
+
+# ---- time-slice charge q(x0, t) and its correlator (Sec. 4, eq. qcorr) ----------------------------
+
+def test_slices_sum_to_q_and_parity_reverses_them():
+    U = I.random_links((3, 3, 4, 5), 3, 0.4)
+    q = O.slice_charge(U, TW, 3)
+    assert q.shape == (5,)
+    assert np.sum(q) == pytest.approx(O.measure(U, TW)["Q"], rel=1e-12, abs=1e-14)
+    qr = O.slice_charge(F.reflect_x3(U), TW, 3)
+    # x3 -> -x3 maps slice x to slice -x and flips the sign of the density
+    assert np.allclose(qr, -q[(-np.arange(5)) % 5], rtol=1e-11, atol=1e-14)
+    q2 = O.slice_charge(U, TW, 2)
+    assert q2.shape == (4,) and np.sum(q2) == pytest.approx(np.sum(q), rel=1e-12, abs=1e-14)
+
+
+def test_constant_abelian_field_has_uniform_slices():
+    L = (4, 4, 4, 4)
+    U = F.unit_field(L)
+    U, f1 = F.abelian_flux(U, 0, 1, 1)
+    U, f2 = F.abelian_flux(U, 2, 3, 2)
+    q = O.slice_charge(U, NOTW, 3)
+    Q = O.measure(U, NOTW)["Q"]
+    assert np.allclose(q, Q / 4, rtol=1e-12)
+
+
+def test_slice_correlator_symmetry_and_sum_rule():
+    rng = np.random.default_rng(1)
+    qs = rng.normal(size=(5, 12)) * 0.05
+    Q = qs.sum(axis=1)
+    C, kept = O.slice_correlator(qs, Q)
+    assert kept == int(np.sum(np.abs(Q) < 0.5))
+    # C(d) = C(T - d) and sum_d C(d) = <Q^2>/T over the kept configurations
+    assert np.allclose(C[1:], C[1:][::-1], rtol=1e-13)
+    keep = np.abs(Q) < 0.5
+    assert np.sum(C) == pytest.approx(np.mean(Q[keep] ** 2) / 12, rel=1e-12)
+    # brute-force double loop for one configuration
+    one, _ = O.slice_correlator(qs[:1], [0.0])
+    for d in range(12):
+        ref = sum(qs[0][(x + d) % 12] * qs[0][x] for x in range(12)) / 12
+        assert one[d] == pytest.approx(ref, rel=1e-13)
+    assert O.slice_correlator(qs, [1.0] * 5) == (None, 0)
