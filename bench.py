@@ -47,6 +47,9 @@ WORKLOADS = {
     "mixed256": dict(l=[4, 6, 8], n=256, amp=None, c=0.3,
                      desc="256 x SU(3) mixed l in {4,6,8} (l x l x 3l x 3l), twist n01=1, amp U[0.2,0.6], RK3 eps=0.01 "
                           "to t=c^2 l^2/8 each"),
+    "l8x16_paper": dict(l=[8], n=16, amp=0.3, c=0.3, long=True,
+                        desc="16 x SU(3) 8x8x24x24, twist n01=1, links exp(i 0.3 omega T) seeds 0-15, RK3 eps=0.01 to "
+                             "the coupling's own scale sqrt(8t)=0.3*3l, t=6.48 (648 steps), E/Q/P every step"),
 }
 
 
@@ -57,7 +60,9 @@ def workload_members(name, rank=0):
     for i in range(w["n"]):
         l = w["l"][i % len(w["l"])]
         seed = rank * w["n"] + i
-        t_end = w["c"] ** 2 * l * l / 8.0
+        # t = c^2 l^2 / 8 with the short extent, or the paper's sqrt(8t) = c * 3l
+        scale = 3 * l if w.get("long") else l
+        t_end = w["c"] ** 2 * scale * scale / 8.0
         out.append(((l, l, 3 * l, 3 * l), seed, w["amp"], t_end))
     return out
 
@@ -149,6 +154,32 @@ class Clocks:
         reasons = sorted({names[i] for r in rows for i in range(4) if "Active" in r[5 + i] and "Not" not in r[5 + i]})
         return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
                 "samples": len(rows), "reasons": reasons}
+
+
+STAGE_SOURCES = ["stage.cu", "su3.cuh", "expm.cuh", "lattice.cuh"]
+
+
+def stage_source_hash():
+    import hashlib
+
+    h = hashlib.sha256()
+    for f in STAGE_SOURCES:
+        h.update(open(os.path.join(ROOT, "paper_2107_03747_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()
+
+
+def stored_traffic(workload, prec):
+    """DRAM bytes per stage launch from the committed ncu capture, or None if that capture is of
+    another workload, precision or kernel source."""
+    path = os.path.join(ROOT, "profiles", "k_stage_traffic.json")
+    try:
+        d = json.load(open(path))
+    except Exception:
+        return None
+    if d.get("workload") != workload or d.get("precision") != prec or d.get("stage_source_sha256") != stage_source_hash():
+        return None
+    b = d.get("dram_bytes_per_launch")
+    return float(sum(b) / len(b)) if b else None
 
 
 def dist_init():
@@ -353,7 +384,10 @@ def run_tgf(args):
     roof = {"kernel": "k_stage (fused staples+force+RK3+exp+update)", "bound": "alu",
             "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
             "peak_source": f"measured {'FP64' if peak_prec == tgf.TGF_FP64 else 'FP32'} FMA-pipe peak (tgf_fma_peak)",
-            "traffic": None, "flop_per_site": STAGE_FLOP, "sites_per_launch": V,
+            "traffic": stored_traffic(args.workload, args.prec), "traffic_unit": "bytes per stage launch (ncu)",
+            "algorithmic_bytes_per_launch": (2240 if prec != tgf.TGF_FP64 else 4480) / 3.0 * V *
+                                             (1.0 if prec != tgf.TGF_FP32_R12 else 1664.0 / 2240.0),
+            "flop_per_site": STAGE_FLOP, "sites_per_launch": V,
             "stage_ms": [stage_ms[1], stage_ms[2], stage_ms[3]],
             "measure_ms": meas_ms, "measure_tflops": MEAS_FLOP * V / (meas_ms * 1e-3) / 1e12}
 
@@ -372,14 +406,18 @@ def run_tgf(args):
         torch.cuda.synchronize()
         ms64 = e0.elapsed_time(e1)
         o64 = obs64.view(len(Ls), cap, 5).cpu().numpy()
-        rel, dq = 0.0, 0.0
+        rel, dq, rel_kept = 0.0, 0.0, 0.0
         for i in range(len(Ls)):
             n = nrec[i]
-            rel = max(rel, float(np.max(np.abs(res_obs[i, :n, 1] / o64[i, :n, 1] - 1))))
+            ri = float(np.max(np.abs(res_obs[i, :n, 1] / o64[i, :n, 1] - 1)))
+            rel = max(rel, ri)
+            if abs(o64[i, n - 1, 2]) < 0.5:  # configurations that enter lambda_TGF
+                rel_kept = max(rel_kept, ri)
             dq = max(dq, float(np.max(np.abs(res_obs[i, :n, 2] - o64[i, :n, 2]))))
         lam64 = lam_of(torch.from_numpy(o64.reshape(-1)), nrec)
         dlam = max(abs(lams[k][0] / lam64[k][0] - 1) for k in lams if lams[k][0] and lam64[k][0])
-        acc = {"max_rel_dE_vs_fp64": rel, "max_abs_dQ_vs_fp64": dq, "rel_dlambda_vs_fp64": dlam,
+        acc = {"max_rel_dE_vs_fp64": rel, "max_rel_dE_vs_fp64_kept": rel_kept, "max_abs_dQ_vs_fp64": dq,
+               "rel_dlambda_vs_fp64": dlam,
                "target_rel_dE": 1e-6, "reunit_every": reunit}
         fp64 = {"value": work / (ms64 * 1e-3), "ms_per_step": ms64, "speedup_of_this_form": ms64 / ms}
         del b64
