@@ -57,7 +57,7 @@ typedef enum {
     TGF_OK = 0,
     TGF_EINVAL = 1,   /* bad argument: extents, twist, sizes, pointers, eps, t_end   */
     TGF_ECUDA = 3,    /* a CUDA runtime call failed (message in tgf_last_error)      */
-    TGF_EKERNEL = 4,  /* a kernel reported an error (non-finite observable)          */
+    TGF_EKERNEL = 4,  /* reserved: kernels report no status (non-finite inputs give NaN records) */
     TGF_ESTATE = 6    /* no configuration survived the |Q| < 1/2 cut                  */
 } tgf_status;
 
