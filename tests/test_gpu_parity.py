@@ -359,3 +359,50 @@ def test_slice_charge_full_size_l16_sums_to_q(tgf):
     Q = b.measure()[0][2]
     assert q.shape == (48,)
     assert q.sum() == pytest.approx(Q, abs=1e-5)
+
+
+# ---- host-buffer path and resumed flows -------------------------------------------------------------
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "fp32_r12"])
+def test_upload_download_through_host_buffers(tgf, prec):
+    """tgf_upload / tgf_download move canonical host fields through a device staging buffer."""
+    import torch
+
+    Ls = [(4, 4, 12, 12), (3, 3, 5, 7), (2, 2, 6, 6)]
+    fields = [I.random_links(L, 90 + i, 0.5) for i, L in enumerate(Ls)]
+    host = torch.from_numpy(np.concatenate([f.view(np.float64).reshape(-1) for f in fields])).pin_memory()
+    b = tgf.FlowBatch(Ls, prec)
+    staging = torch.empty(max(L[0] * L[1] * L[2] * L[3] for L in Ls) * 72, dtype=torch.float64, device="cuda")
+    tgf.tgf_upload(b.prec, b.lat, host, staging, b.links)
+    ref = b.get_links()
+    out = torch.zeros_like(host).pin_memory()
+    tgf.tgf_download(b.prec, b.lat, b.links, staging, out)
+    flat = out.numpy()
+    off = 0
+    for L, r, f in zip(Ls, ref, fields):
+        n = L[0] * L[1] * L[2] * L[3] * 72
+        got = flat[off:off + n].view(np.complex128).reshape(r.shape)
+        assert np.array_equal(got, r)
+        if prec == "fp64":
+            assert np.array_equal(got, f)
+        off += n
+    small = torch.empty(16, dtype=torch.float64, device="cuda")
+    with pytest.raises(tgf.TgfError):
+        tgf.tgf_upload(b.prec, b.lat, host, small, b.links)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_resumed_flow_is_bitwise_identical(tgf, prec):
+    """Flowing to t1 and then, from the resulting field, for t2 - t1 reproduces one flow to t2 (no
+    re-projection scheduled): the state of the flow between steps is the field alone."""
+    L = (4, 4, 12, 12)
+    U = I.random_links(L, 95, 0.5)
+    a = load(tgf, [L], [U], prec)
+    oa, na = a.flow(0.01, 0.10)
+    b = load(tgf, [L], [U], prec)
+    ob1, nb1 = b.flow(0.01, 0.04)
+    ob2, nb2 = b.flow(0.01, 0.06)
+    assert np.array_equal(a.get_links()[0], b.get_links()[0])
+    ra = oa.cpu().numpy()[0, : na[0]]
+    rb = np.concatenate([ob1.cpu().numpy()[0, : nb1[0] - 1], ob2.cpu().numpy()[0, : nb2[0]]])
+    assert np.array_equal(ra[:, 1:], rb[:, 1:])
