@@ -183,6 +183,28 @@ tgf_status tgf_flow(int prec, const tgf_lattice *lat, int ncfg, void *w, void *w
 /* Number of records tgf_flow writes for one configuration (host arithmetic only). */
 tgf_status tgf_flow_records(double eps, double t_end, int measure_every, int *n_records);
 
+/* ---- ensemble generation (Sec. 3.1) ------------------------------------------------------ */
+
+/* n_hybrid hybrid Monte Carlo sweeps of every configuration of `links` (TGF_FP64 storage), in
+ * place: each is one heat-bath sweep followed by n_or over-relaxation sweeps, the algorithm the
+ * paper uses to generate its ensembles (Sec. 3.1: one heat-bath sweep, then L~ over-relaxation
+ * sweeps).  The action is the twisted Wilson action with beta = 18 b = 6/g0^2, so the weight of
+ * a link U is exp((beta/3) Re Tr[U Sigma]), Sigma its twisted staple sum.  SU(3) is updated in
+ * its three SU(2) subgroups (0,1), (0,2), (1,2) (Cabibbo-Marinari): heat-bath R = X v^+ with
+ * X0 drawn by Kennedy-Pendleton (alpha > 2) or Creutz (otherwise), alpha = 2 beta k / 3;
+ * over-relaxation R = (v^+)^2; U <- R U.  A sweep visits mu = 0..3, and for each the sites of
+ * parity 0 then 1 (x0+x1+x2+x3 mod 2), so every extent must be even.
+ * Random numbers are counter-based and reproducible: configuration c (index in this call) uses
+ * key = h(seed, c), and draw `slot` of SU(2) subgroup g of link (site, mu) in heat-bath sweep
+ * number w = first_sweep + h is h(key, (((w*4 + mu)*V + site)*3 + g)*260 + slot) with h(k, i) the
+ * SplitMix64 output function of k + (i + 1) * 0x9E3779B97F4A7C15, mapped to
+ * ((x >> 11) + 1) * 2^-53 in (0, 1]; slots 4a..4a+3 serve rejection attempt a < 64, slots 256
+ * and 257 the direction of X; a subgroup with 64 rejected attempts is left unchanged.
+ * Errors: TGF_EINVAL for another precision, an odd extent, beta <= 0 or not finite, negative
+ * counts.  Enqueues 8 (1 + n_or) n_hybrid launches on `stream`. */
+tgf_status tgf_mc_sweeps(int prec, const tgf_lattice *lat, int ncfg, void *links, double beta, int n_hybrid,
+                         int n_or, unsigned long long seed, unsigned long long first_sweep, void *stream);
+
 /* ---- coupling (host only) ----------------------------------------------------------------- */
 
 /* N(c, Lt) of eq. (latt_norm) for SU(N): the inverse of

@@ -63,6 +63,7 @@ _SIGS = {
     "tgf_slice_correlator": [C.POINTER(C.c_double), _SZ, C.POINTER(C.c_double), C.c_int, C.c_int,
                              C.POINTER(C.c_double), C.POINTER(C.c_int)],
     "tgf_measure_noalloc": [C.c_int, _LATP, C.c_int, _P, _P, _SZ, C.c_int, C.c_double, C.c_uint, _P],
+    "tgf_mc_sweeps": [C.c_int, _LATP, C.c_int, _P, C.c_double, C.c_int, C.c_int, C.c_ulonglong, C.c_ulonglong, _P],
     "tgf_norm": [C.c_double, C.c_int, C.c_int, C.POINTER(C.c_double)],
     "tgf_fma_peak": [C.c_int, _P, C.c_int, C.c_int, C.POINTER(C.c_double), _P],
     "tgf_lambda": [C.c_double, C.c_int, C.c_double, C.POINTER(C.c_double), C.POINTER(C.c_double), C.c_int,
@@ -237,6 +238,12 @@ def tgf_fma_peak(prec, blocks_per_sm=8, iters=4096, stream=None) -> float:
     out = C.c_double()
     _check(_lib.tgf_fma_peak(prec, _ptr(sink), blocks_per_sm, iters, C.byref(out), _stream(stream)))
     return out.value
+
+
+def tgf_mc_sweeps(prec, lat, links, beta, n_hybrid, n_or, seed, first_sweep, stream=None):
+    """n_hybrid hybrid sweeps (1 heat-bath + n_or over-relaxation each) of FP64 `links`, in place."""
+    _check(_lib.tgf_mc_sweeps(prec, lat, len(lat), _ptr(links), float(beta), int(n_hybrid), int(n_or),
+                              int(seed) & 0xFFFFFFFFFFFFFFFF, int(first_sweep), _stream(stream)))
 
 
 def tgf_norm(c, Lt, N=3) -> float:

@@ -406,6 +406,35 @@ tgf_status tgf_measure(int prec, const tgf_lattice* lat, int ncfg, const void* l
                            (cudaStream_t)stream);
 }
 
+tgf_status tgf_mc_sweeps(int prec, const tgf_lattice* lat, int ncfg, void* links, double beta, int n_hybrid, int n_or,
+                         unsigned long long seed, unsigned long long first_sweep, void* stream) {
+    tgf_status s;
+    if ((s = check_lat(lat, ncfg)) || (s = check_ptr(links, "links"))) return s;
+    if (prec != TGF_FP64) return fail(TGF_EINVAL, "the Monte Carlo update needs TGF_FP64 storage (got precision %d)", prec);
+    for (int c = 0; c < ncfg; ++c)
+        for (int mu = 0; mu < 4; ++mu)
+            if (lat[c].L[mu] % 2)
+                return fail(TGF_EINVAL, "configuration %d: extent L[%d] = %d is odd (checkerboard update)", c, mu,
+                            lat[c].L[mu]);
+    if (!(std::isfinite(beta) && beta > 0.0)) return fail(TGF_EINVAL, "beta = %g must be finite and positive", beta);
+    if (n_hybrid < 0 || n_or < 0) return fail(TGF_EINVAL, "n_hybrid = %d and n_or = %d must be >= 0", n_hybrid, n_or);
+    Layout Ly = layout(prec, lat, ncfg);
+    Batch B = make_batch(lat, Ly, all_cfgs(ncfg), 256);
+    cudaStream_t st = (cudaStream_t)stream;
+    for (int h = 0; h < n_hybrid; ++h) {
+        for (int o = -1; o < n_or; ++o) {
+            const int overrelax = o >= 0;
+            for (int mu = 0; mu < 4; ++mu)
+                for (int parity = 0; parity < 2; ++parity) {
+                    launch_mc(overrelax, B, static_cast<double*>(links), mu, parity, beta, (uint64_t)seed,
+                              (uint64_t)(first_sweep + (unsigned long long)h), st);
+                    if ((s = last_launch(overrelax ? "over-relaxation" : "heat-bath"))) return s;
+                }
+        }
+    }
+    return TGF_OK;
+}
+
 tgf_status tgf_measure_slices(int prec, const tgf_lattice* lat, int ncfg, const void* links, double* scratch,
                               size_t scratch_bytes, int dir, double* q_dev, size_t q_stride, unsigned flags,
                               void* stream) {

@@ -211,6 +211,11 @@ void launch_reduce(const Batch& B, const double* partial, double* obs, cudaStrea
 void launch_slice_charge(int prec, unsigned flags, const Batch& B, const void* clov, int dir, double* q, int q_stride,
                          cudaStream_t st);
 void launch_pack(int prec, const Batch& B, const double* canon, void* w, cudaStream_t st);
+// one checkerboard pass of the Monte Carlo update (FP64 storage): links of direction mu on the
+// sites of the given parity; heat-bath (overrelax = 0) or over-relaxation; the batch has
+// ceil(V / 256) blocks of 128 threads per configuration
+void launch_mc(int overrelax, const Batch& B, double* w, int mu, int parity, double beta, uint64_t seed,
+               uint64_t sweep, cudaStream_t st);
 void launch_unpack(int prec, const Batch& B, const void* w, double* canon, cudaStream_t st);
 
 constexpr int kMeasureSites = 128;  // sites (threads) per block of the measurement kernel

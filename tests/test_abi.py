@@ -135,3 +135,22 @@ def test_slice_correlator_matches_oracle(lib):
     assert kept == ko
     assert np.allclose(C, Co, rtol=1e-13, atol=1e-16)
     assert lib.tgf_slice_correlator(q, [0.9] * 6) == (None, 0)
+
+
+@pytest.mark.parametrize("bad", ["prec", "odd", "beta", "count", "align"])
+def test_mc_bad_arguments_are_rejected_before_device_work(lib, bad):
+    lat = lib.lattices([(4, 4, 12, 12)])
+    ptr, prec, beta, nh = 1 << 20, lib.TGF_FP64, 6.0, 1
+    if bad == "prec":
+        prec = lib.TGF_FP32
+    elif bad == "odd":
+        lat = lib.lattices([(4, 4, 12, 11)])
+    elif bad == "beta":
+        beta = 0.0
+    elif bad == "count":
+        nh = -1
+    elif bad == "align":
+        ptr += 8
+    s = lib._lib.tgf_mc_sweeps(prec, lat, 1, ptr, beta, nh, 1, 0, 0, None)
+    assert s == lib.TGF_EINVAL
+    assert len(lib._lib.tgf_last_error()) > 0

@@ -1,0 +1,83 @@
+"""End to end against a number the paper prints: lambda_TGF at L~ = 12, 18b = 20 (Table B.1).
+
+Ensembles are generated on the GPU with the paper's hybrid algorithm (tgf_mc_sweeps: one
+heat-bath sweep and L~ over-relaxation sweeps per hybrid sweep, L~ hybrid sweeps between
+measurements, Sec. 3.1), 256 independent chains started at the twist-eater (the classical
+minimum of the twisted action).  Each measurement flows the configuration to sqrt(8t) = c L~
+(c = 0.3, t = 1.62) in FP32 and takes the clover E and Q there; lambda_TGF = N(c, L~) t^2
+<E d_Q> / (3 <d_Q>) (eq. lambdat_latt) with the lattice normalisation of eq. (latt_norm).
+The statistical error is a jackknife over chains; the test accepts the printed value within
+four combined standard deviations.  This pins, at once, the action and its twist factors, the
+Monte Carlo weight, the flow, the clover energy density, the topological cut and N(c, L~).
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+from paper_2107_03747_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+def printed(beta, Lt):
+    for line in open(os.path.join(HERE, "golden", "table_b1.txt")):
+        if line.startswith("#") or not line.strip():
+            continue
+        b, l, lam, err = line.split()
+        if float(b) == beta and int(l) == Lt:
+            return float(lam), float(err)
+    raise KeyError((beta, Lt))
+
+
+def generate_and_measure(tgf, beta, l=4, chains=256, therm=50, rounds=16, c=0.3, seed=2107):
+    import torch
+
+    L = I.tgf_extent(l)
+    Lt = 3 * l
+    t = (c * Lt) ** 2 / 8.0
+    mc = tgf.FlowBatch([L] * chains, "fp64")
+    mc.set_links([I.twist_eater(L, 1)] * chains)
+    fl = tgf.FlowBatch([L] * chains, "fp32")
+    canon = torch.empty(mc.canonical_numel(), dtype=torch.float64, device=mc.device)
+    sweep = 0
+    tgf.tgf_mc_sweeps(mc.prec, mc.lat, mc.links, beta, therm, Lt, seed, sweep)
+    sweep += therm
+    E = np.zeros((rounds, chains))
+    Q = np.zeros((rounds, chains))
+    for r in range(rounds):
+        tgf.tgf_mc_sweeps(mc.prec, mc.lat, mc.links, beta, Lt, Lt, seed, sweep)
+        sweep += Lt
+        tgf.tgf_unpack(mc.prec, mc.lat, mc.links, canon)
+        tgf.tgf_pack(fl.prec, fl.lat, canon, fl.links)
+        obs, nrec = fl.flow(0.01, t, measure_every=1 << 20)
+        o = obs.cpu().numpy()
+        last = np.asarray(nrec) - 1
+        E[r] = o[np.arange(chains), last, 1]
+        Q[r] = o[np.arange(chains), last, 2]
+        assert np.allclose(o[np.arange(chains), last, 0], t)
+    return Lt, t, E, Q
+
+
+def jackknife_lambda(tgf, c, Lt, t, E, Q):
+    lam = tgf.tgf_lambda(c, Lt, t, E.ravel(), Q.ravel())[0]
+    n = E.shape[1]
+    jk = np.array([tgf.tgf_lambda(c, Lt, t, np.delete(E, j, axis=1).ravel(), np.delete(Q, j, axis=1).ravel())[0]
+                   for j in range(n)])
+    err = math.sqrt((n - 1) / n * np.sum((jk - jk.mean()) ** 2))
+    return lam, err
+
+
+def test_lambda_tgf_at_Lt12_beta20_matches_table_b1(tgf):
+    beta = 20.0
+    Lt, t, E, Q = generate_and_measure(tgf, beta)
+    lam, err = jackknife_lambda(tgf, 0.3, Lt, t, E, Q)
+    ref, ref_err = printed(beta, Lt)
+    sigma = math.sqrt(err ** 2 + ref_err ** 2)
+    print(f"lambda_TGF(L~=12, 18b=20): {lam:.5f} +- {err:.5f} (paper {ref} +- {ref_err}); "
+          f"kept {int(np.sum(np.abs(Q) < 0.5))}/{Q.size}; {abs(lam - ref) / sigma:.2f} sigma")
+    assert err < 0.01 * lam
+    assert abs(lam - ref) < 4 * sigma
