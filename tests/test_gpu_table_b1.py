@@ -1,4 +1,4 @@
-"""End to end against a number the paper prints: lambda_TGF at L~ = 12, 18b = 20 (Table B.1).
+"""End to end against numbers the paper prints: lambda_TGF at L~ = 12, 18b = 20 and 8 (Table B.1).
 
 Ensembles are generated on the GPU with the paper's hybrid algorithm (tgf_mc_sweeps: one
 heat-bath sweep and L~ over-relaxation sweeps per hybrid sweep, L~ hybrid sweeps between
@@ -71,13 +71,15 @@ def jackknife_lambda(tgf, c, Lt, t, E, Q):
     return lam, err
 
 
-def test_lambda_tgf_at_Lt12_beta20_matches_table_b1(tgf):
-    beta = 20.0
-    Lt, t, E, Q = generate_and_measure(tgf, beta)
+@pytest.mark.parametrize("beta,therm", [(20.0, 50), (8.0, 150)])
+def test_lambda_tgf_at_Lt12_matches_table_b1(tgf, beta, therm):
+    Lt, t, E, Q = generate_and_measure(tgf, beta, therm=therm)
     lam, err = jackknife_lambda(tgf, 0.3, Lt, t, E, Q)
     ref, ref_err = printed(beta, Lt)
     sigma = math.sqrt(err ** 2 + ref_err ** 2)
-    print(f"lambda_TGF(L~=12, 18b=20): {lam:.5f} +- {err:.5f} (paper {ref} +- {ref_err}); "
-          f"kept {int(np.sum(np.abs(Q) < 0.5))}/{Q.size}; {abs(lam - ref) / sigma:.2f} sigma")
+    half = [jackknife_lambda(tgf, 0.3, Lt, t, E[h::2], Q[h::2])[0] for h in (0, 1)]
+    print(f"lambda_TGF(L~={Lt}, 18b={beta}): {lam:.5f} +- {err:.5f} (paper {ref} +- {ref_err}); "
+          f"kept {int(np.sum(np.abs(Q) < 0.5))}/{Q.size}; {abs(lam - ref) / sigma:.2f} sigma; "
+          f"even/odd rounds {half[0]:.5f} {half[1]:.5f}")
     assert err < 0.01 * lam
     assert abs(lam - ref) < 4 * sigma
