@@ -1,6 +1,7 @@
 """End to end against numbers the paper prints: lambda_TGF at L~ = 12, 18b = 20 and 8 (Table B.1).
 
-Ensembles are generated on the GPU with the paper's hybrid algorithm (tgf_mc_sweeps: one
+Ensembles are generated on the GPU (paper_2107_03747_gb300.ensemble) with the paper's hybrid
+algorithm (tgf_mc_sweeps: one
 heat-bath sweep and L~ over-relaxation sweeps per hybrid sweep, L~ hybrid sweeps between
 measurements, Sec. 3.1), 256 independent chains started at the twist-eater (the classical
 minimum of the twisted action).  Each measurement flows the configuration to sqrt(8t) = c L~
@@ -16,7 +17,6 @@ import os
 import numpy as np
 import pytest
 
-from paper_2107_03747_gb300 import inputs as I
 
 pytestmark = pytest.mark.gpu
 
@@ -33,51 +33,15 @@ def printed(beta, Lt):
     raise KeyError((beta, Lt))
 
 
-def generate_and_measure(tgf, beta, l=4, chains=256, therm=50, rounds=16, c=0.3, seed=2107):
-    import torch
-
-    L = I.tgf_extent(l)
-    Lt = 3 * l
-    t = (c * Lt) ** 2 / 8.0
-    mc = tgf.FlowBatch([L] * chains, "fp64")
-    mc.set_links([I.twist_eater(L, 1)] * chains)
-    fl = tgf.FlowBatch([L] * chains, "fp32")
-    canon = torch.empty(mc.canonical_numel(), dtype=torch.float64, device=mc.device)
-    sweep = 0
-    tgf.tgf_mc_sweeps(mc.prec, mc.lat, mc.links, beta, therm, Lt, seed, sweep)
-    sweep += therm
-    E = np.zeros((rounds, chains))
-    Q = np.zeros((rounds, chains))
-    for r in range(rounds):
-        tgf.tgf_mc_sweeps(mc.prec, mc.lat, mc.links, beta, Lt, Lt, seed, sweep)
-        sweep += Lt
-        tgf.tgf_unpack(mc.prec, mc.lat, mc.links, canon)
-        tgf.tgf_pack(fl.prec, fl.lat, canon, fl.links)
-        obs, nrec = fl.flow(0.01, t, measure_every=1 << 20)
-        o = obs.cpu().numpy()
-        last = np.asarray(nrec) - 1
-        E[r] = o[np.arange(chains), last, 1]
-        Q[r] = o[np.arange(chains), last, 2]
-        assert np.allclose(o[np.arange(chains), last, 0], t)
-    return Lt, t, E, Q
-
-
-def jackknife_lambda(tgf, c, Lt, t, E, Q):
-    lam = tgf.tgf_lambda(c, Lt, t, E.ravel(), Q.ravel())[0]
-    n = E.shape[1]
-    jk = np.array([tgf.tgf_lambda(c, Lt, t, np.delete(E, j, axis=1).ravel(), np.delete(Q, j, axis=1).ravel())[0]
-                   for j in range(n)])
-    err = math.sqrt((n - 1) / n * np.sum((jk - jk.mean()) ** 2))
-    return lam, err
-
-
 @pytest.mark.parametrize("beta,therm", [(20.0, 50), (8.0, 150)])
 def test_lambda_tgf_at_Lt12_matches_table_b1(tgf, beta, therm):
-    Lt, t, E, Q = generate_and_measure(tgf, beta, therm=therm)
-    lam, err = jackknife_lambda(tgf, 0.3, Lt, t, E, Q)
+    from paper_2107_03747_gb300 import ensemble
+
+    Lt, t, E, Q = ensemble.generate_and_measure(beta, l=4, chains=256, therm=therm, rounds=16, c=0.3, seed=2107)
+    lam, err = ensemble.jackknife_lambda(0.3, Lt, t, E, Q)
     ref, ref_err = printed(beta, Lt)
     sigma = math.sqrt(err ** 2 + ref_err ** 2)
-    half = [jackknife_lambda(tgf, 0.3, Lt, t, E[h::2], Q[h::2])[0] for h in (0, 1)]
+    half = [ensemble.jackknife_lambda(0.3, Lt, t, E[h::2], Q[h::2])[0] for h in (0, 1)]
     print(f"lambda_TGF(L~={Lt}, 18b={beta}): {lam:.5f} +- {err:.5f} (paper {ref} +- {ref_err}); "
           f"kept {int(np.sum(np.abs(Q) < 0.5))}/{Q.size}; {abs(lam - ref) / sigma:.2f} sigma; "
           f"even/odd rounds {half[0]:.5f} {half[1]:.5f}")
