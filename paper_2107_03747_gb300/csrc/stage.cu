@@ -64,6 +64,9 @@ constexpr int stage_min_blocks() { return P == P64 ? 2 : TGF_STAGE_MINB32; }
 // pair up in the topological charge); -1 for mu >= nu.
 __constant__ int8_t c_plane_of[4][4] = {{-1, 0, 2, 4}, {-1, -1, 5, 3}, {-1, -1, -1, 1}, {-1, -1, -1, -1}};
 __constant__ int8_t c_pair[6][2] = {{0, 1}, {2, 3}, {0, 2}, {1, 3}, {0, 3}, {1, 2}};
+// Which direction's warp builds the clover halves of each plane: 01, 02 by warp 0; 12, 13 by
+// warp 1; 23 by warp 2; 03 by warp 3 -- two planes at most per warp instead of 3, 2, 1, 0.
+__constant__ int8_t c_clover_owner[4][4] = {{0, 1, 1, 0}, {0, 0, 1, 1}, {0, 0, 0, 1}, {1, 0, 0, 0}};
 
 // The anti-Hermitian part D - D^+ of a 3x3 matrix as 9 reals (2 Im D_jj; D_jk - conj(D_kj), j<k),
 // written to 9 component planes of length Vp.
@@ -87,8 +90,8 @@ __device__ __forceinline__ void store_ah(T* __restrict__ p, int Vp, int s, const
 // direction nu (below), the four leaves of eq. (gmunu) are L1 = U F, L2 = B^+ U^+ (both from
 // link (n, mu)) and L3 = F' U', L4 = U'^+ B'^+ (from link (n - mu, mu), primed), so
 //   C - C^+ = [D1 - D1^+] + [D2 - D2^+],  D1 = U (F - B) at n,  D2 = (F' - B') U' carried to n.
-// Thread (n, mu) writes D1 - D1^+ to site n and D (F - B) U - h.c. to site n + mu, for nu > mu,
-// plus Re Tr(U F) (the twisted plaquette at n).
+// Thread (n, mu) writes D1 - D1^+ to site n and D2 - D2^+ to site n + mu for the planes its warp
+// builds (c_clover_owner), plus Re Tr(U F) (the twisted plaquette at n).
 template <int P, int STAGE, int MODE, int SPB, int CAP>
 __global__ void __launch_bounds__(4 * SPB, stage_min_blocks<P>())
 k_stage(const __grid_constant__ BatchT<CAP> B, const typename Store<P>::T* __restrict__ w_in,
@@ -138,7 +141,7 @@ k_stage(const __grid_constant__ BatchT<CAP> B, const typename Store<P>::T* __res
 #pragma unroll 1
         for (int dn = 1; dn < 4; ++dn) {
             const int nu = (mu + dn) & 3;
-            const bool clover = MODE != 0 && nu > mu;
+            const bool clover = MODE != 0 && c_clover_owner[mu][nu];
             if (MODE == 2 && !clover) continue;
             const int xn = coord(xp, nu), Ln = c.L[nu], Sn = c.st[nu];
             const int s_nm = step_m(s, xn, Ln, Sn);
@@ -192,7 +195,7 @@ k_stage(const __grid_constant__ BatchT<CAP> B, const typename Store<P>::T* __res
                 mul_dn_acc(sig, t, a);
             }
             if (clover) {
-                const int pl = c_plane_of[mu][nu];
+                const int pl = c_plane_of[mu < nu ? mu : nu][mu < nu ? nu : mu];
                 T* cb = clov + c.m_off;
                 link(mu, s, a);  // U = U_mu(n)
                 // Re Tr(U F): the twisted plaquette Z* P_{mu nu}(n)
@@ -203,13 +206,16 @@ k_stage(const __grid_constant__ BatchT<CAP> B, const typename Store<P>::T* __res
                     for (int j = 0; j < 3; ++j)
                         rt += a.e[i][j].re * f.e[j][i].re - a.e[i][j].im * f.e[j][i].im;
                 cb[(size_t)(108 + pl) * Vp + s] = rt;
-                // K = F - B; D1 = U K (site n), D2 = K U (site n + mu)
+                // K = F - B; D1 = U K (site n), D2 = K U (site n + mu).  A plane built through its
+                // second direction (nu < mu) takes K = B - F: the leaves of the plane (mu, nu) are the
+                // Hermitian conjugates of those of (nu, mu), so its C - C^+ changes sign.
+                const T sg = nu > mu ? T(1) : T(-1);
 #pragma unroll
                 for (int i = 0; i < 3; ++i)
 #pragma unroll
                     for (int j = 0; j < 3; ++j) {
-                        f.e[i][j].re -= b.e[i][j].re;
-                        f.e[i][j].im -= b.e[i][j].im;
+                        f.e[i][j].re = sg * (f.e[i][j].re - b.e[i][j].re);
+                        f.e[i][j].im = sg * (f.e[i][j].im - b.e[i][j].im);
                     }
                 mul_nn(t, a, f);
                 store_ah(cb + (size_t)(pl * 2 + 0) * 9 * Vp, Vp, s, t);
