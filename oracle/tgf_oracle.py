@@ -16,7 +16,8 @@ Conventions (Sec. 3.1 of arXiv:2107.03747):
   * a link field is a complex128 array of shape ``(L3, L2, L1, L0, 4, 3, 3)``
     (x0 fastest, then mu, row, col); ``U[..., mu, :, :]`` is U_mu(n);
   * the twist tensor ``n`` is an antisymmetric integer 4x4 array; the plaquette
-    factor Z_{mu nu}(n) = exp(2 pi i n_{mu nu} / 3) at the plaquettes whose
+    factor Z_{mu nu}(n) = exp(2 pi i n_{mu nu} / N) (N = 3 for the paper's SU(3); every
+    function takes N from the field's last axis) at the plaquettes whose
     corner has x_mu = c_mu and x_nu = c_nu (``corner``, default the origin,
     the 0-based reading of "x_1 = x_2 = 1"), and 1 everywhere else.
 """
@@ -75,18 +76,18 @@ def coords(L):
     return [x0, x1, x2, x3]
 
 
-def twist_factor(L, twist, mu: int, nu: int, corner=(0, 0, 0, 0)) -> np.ndarray:
+def twist_factor(L, twist, mu: int, nu: int, corner=(0, 0, 0, 0), N: int = NC) -> np.ndarray:
     """Z_{mu nu}(n) over all sites (Sec. 3.1, the centre factor of the twisted plaquettes).
 
-    Z_{mu nu} = exp(2 pi i n_{mu nu} / 3) where x_mu = corner_mu and x_nu = corner_nu,
+    Z_{mu nu} = exp(2 pi i n_{mu nu} / N) where x_mu = corner_mu and x_nu = corner_nu,
     and 1 elsewhere; Z_{nu mu} = Z_{mu nu}^* follows from n antisymmetric.
     """
     x = coords(L)
     z = np.ones(x[0].shape, dtype=np.complex128)
-    k = int(twist[mu][nu]) % NC
+    k = int(twist[mu][nu]) % N
     if k != 0 and mu != nu:
         where = (x[mu] == corner[mu]) & (x[nu] == corner[nu])
-        z[where] = np.exp(2j * math.pi * int(twist[mu][nu]) / NC)
+        z[where] = np.exp(2j * math.pi * int(twist[mu][nu]) / N)
     return z[..., None, None]
 
 
@@ -107,12 +108,13 @@ def reduced_action(U: np.ndarray, twist, corner=(0, 0, 0, 0)) -> float:
     """
     L = extents_of(U)
     Ud = links_by_dir(U)
+    N = U.shape[-1]
     s = 0.0
     for mu in range(4):
         for nu in range(mu + 1, 4):
-            z = twist_factor(L, twist, mu, nu, corner)
+            z = twist_factor(L, twist, mu, nu, corner, N)
             zp = np.conj(z) * plaquette(Ud, mu, nu)
-            s += float(np.sum(np.real(tr(np.eye(NC) - zp))))
+            s += float(np.sum(np.real(tr(np.eye(N) - zp))))
     return s
 
 
@@ -125,8 +127,8 @@ def wilson_action_ordered(U: np.ndarray, twist, corner=(0, 0, 0, 0)) -> float:
         for nu in range(4):
             if mu == nu:
                 continue
-            z = twist_factor(L, twist, mu, nu, corner)
-            s += np.sum(tr(np.eye(NC) - np.conj(z) * plaquette(Ud, mu, nu)))
+            z = twist_factor(L, twist, mu, nu, corner, U.shape[-1])
+            s += np.sum(tr(np.eye(U.shape[-1]) - np.conj(z) * plaquette(Ud, mu, nu)))
     return complex(s)
 
 
@@ -136,8 +138,9 @@ def wilson_action_ordered(U: np.ndarray, twist, corner=(0, 0, 0, 0)) -> float:
 
 def proj_ta(M: np.ndarray) -> np.ndarray:
     """Traceless anti-Hermitian part: (M - M^+)/2 - tr(M - M^+)/(2N) * 1."""
+    N = M.shape[-1]
     A = 0.5 * (M - dag(M))
-    return A - (tr(A) / NC)[..., None, None] * np.eye(NC)
+    return A - (tr(A) / N)[..., None, None] * np.eye(N)
 
 
 def staple_sum(Ud, L, twist, mu: int, corner=(0, 0, 0, 0)) -> np.ndarray:
@@ -152,7 +155,7 @@ def staple_sum(Ud, L, twist, mu: int, corner=(0, 0, 0, 0)) -> np.ndarray:
     for nu in range(4):
         if nu == mu:
             continue
-        z = twist_factor(L, twist, mu, nu, corner)
+        z = twist_factor(L, twist, mu, nu, corner, Ud[mu].shape[-1])
         fwd = np.conj(z) * mm(shift(Ud[nu], mu, 1), dag(shift(Ud[mu], nu, 1)), dag(Ud[nu]))
         z_m = shift(z, nu, -1)
         Unu_m = shift(Ud[nu], nu, -1)
@@ -193,7 +196,7 @@ def expm(X: np.ndarray) -> np.ndarray:
     for sv in np.unique(s):
         sel = s == sv
         Y = X[sel] / (2.0 ** sv)
-        T = np.broadcast_to(np.eye(NC, dtype=X.dtype), Y.shape).copy()
+        T = np.broadcast_to(np.eye(X.shape[-1], dtype=X.dtype), Y.shape).copy()
         term = T.copy()
         for k in range(1, 31):
             term = np.matmul(term, Y) / k
@@ -248,7 +251,7 @@ def clover(Ud, L, twist, mu: int, nu: int, corner=(0, 0, 0, 0)) -> np.ndarray:
 
     with U_{-mu}(n) = U_mu(n-mu)^+ and Z = Z_{mu nu}.
     """
-    z = twist_factor(L, twist, mu, nu, corner)
+    z = twist_factor(L, twist, mu, nu, corner, Ud[mu].shape[-1])
     Um, Un = Ud[mu], Ud[nu]
     l1 = np.conj(z) * mm(Um, shift(Un, mu, 1), dag(shift(Um, nu, 1)), dag(Un))
     Un_mn = shift(Un, nu, -1)  # U_nu(n-nu)
@@ -276,7 +279,7 @@ def field_strength(U: np.ndarray, twist, traceless: bool = False, corner=(0, 0, 
             C = clover(Ud, L, twist, mu, nu, corner)
             g = (-1j / 8.0) * (C - dag(C))
             if traceless:
-                g = g - (tr(g) / NC)[..., None, None] * np.eye(NC)
+                g = g - (tr(g) / g.shape[-1])[..., None, None] * np.eye(g.shape[-1])
             G[mu][nu] = g
     return G
 
@@ -325,8 +328,8 @@ def measure(U: np.ndarray, twist, traceless: bool = False, corner=(0, 0, 0, 0)) 
     p = 0.0
     for mu in range(4):
         for nu in range(mu + 1, 4):
-            z = twist_factor(L, twist, mu, nu, corner)
-            p += float(np.sum(np.real(tr(np.conj(z) * plaquette(Ud, mu, nu))))) / 3.0
+            z = twist_factor(L, twist, mu, nu, corner, U.shape[-1])
+            p += float(np.sum(np.real(tr(np.conj(z) * plaquette(Ud, mu, nu))))) / U.shape[-1]
     return {
         "E": e / V,
         "Q": float(np.real(q)) / (16.0 * math.pi ** 2),

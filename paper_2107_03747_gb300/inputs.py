@@ -90,15 +90,47 @@ def random_su3(seed: int, n: int, amp: float, offset: int = 0, device: str = "cp
     return _expi(h, amp, device)
 
 
+def sun_generators(N: int) -> np.ndarray:
+    """Generalised Gell-Mann matrices lambda_a of SU(N), shape (N^2 - 1, N, N), Tr(l_a l_b) = 2 delta_ab
+    (for N = 3 exactly ``gell_mann()``): the symmetric and antisymmetric off-diagonal ones for each
+    pair j < k, then the diagonal ones."""
+    if N == 3:
+        return gell_mann()
+    g = []
+    for j in range(N):
+        for k in range(j + 1, N):
+            a = np.zeros((N, N), dtype=np.complex128)
+            a[j, k] = a[k, j] = 1
+            b = np.zeros((N, N), dtype=np.complex128)
+            b[j, k], b[k, j] = -1j, 1j
+            g += [a, b]
+    for m in range(1, N):
+        d = np.zeros((N, N), dtype=np.complex128)
+        d[np.arange(m), np.arange(m)] = 1
+        d[m, m] = -m
+        g.append(d * math.sqrt(2.0 / (m * (m + 1))))
+    return np.array(g)
+
+
+def random_sun(seed: int, n: int, amp: float, N: int, offset: int = 0, device: str = "cpu") -> np.ndarray:
+    """``n`` SU(N) matrices exp(i*amp*omega_a*lambda_a/2), N^2 - 1 Gaussian omegas each."""
+    if N == 3:
+        return random_su3(seed, n, amp, offset, device)
+    na = N * N - 1
+    om = gaussians(seed, na * n, offset).reshape(n, na)
+    h = np.einsum("na,aij->nij", om, sun_generators(N) * 0.5)
+    return _expi(h, amp, device)
+
+
 def n_sites(L) -> int:
     return int(L[0]) * int(L[1]) * int(L[2]) * int(L[3])
 
 
-def random_links(L, seed: int, amp: float, device: str = "cpu", offset: int = 0) -> np.ndarray:
-    """A random link field in canonical layout (see module docstring)."""
+def random_links(L, seed: int, amp: float, device: str = "cpu", offset: int = 0, N: int = 3) -> np.ndarray:
+    """A random SU(N) link field in canonical layout (see module docstring)."""
     L0, L1, L2, L3 = (int(x) for x in L)
     n = n_sites(L) * 4
-    return random_su3(seed, n, amp, offset, device).reshape(L3, L2, L1, L0, 4, 3, 3)
+    return random_sun(seed, n, amp, N, offset, device).reshape(L3, L2, L1, L0, 4, N, N)
 
 
 def batched_amplitude(seed: int) -> float:
@@ -112,21 +144,31 @@ def batched_member(seed: int, L, device: str = "cpu"):
     return amp, random_links(L, seed, amp, device=device, offset=1)
 
 
-def twist_matrices(k: int = 1):
-    """Clock Gamma_1 = diag(1, w, w^2) and shift Gamma_2 (e_j -> e_{j+1}), w = exp(2 pi i k/3).
+def twist_matrices(k: int = 1, N: int = 3):
+    """Clock Gamma_1 = diag(1, w, ..., w^{N-1}) and shift Gamma_2 (e_j -> e_{j+1}), w = exp(2 pi i k/N).
 
     They satisfy Gamma_1 Gamma_2 = w Gamma_2 Gamma_1, the consistency condition of
-    the twist (Sec. 1, Z_12 = exp(2 pi i k / N) with N = 3).
+    the twist (Sec. 1, Z_12 = exp(2 pi i k / N)).  For even N each is multiplied by an N-th
+    root of its inverse determinant so that both lie in SU(N) (a centre phase, which leaves the
+    commutation relation unchanged); for N = 3 both determinants are already 1.
     """
-    w = np.exp(2j * math.pi * k / 3)
-    g1 = np.diag([1, w, w * w]).astype(np.complex128)
-    g2 = np.zeros((3, 3), dtype=np.complex128)
-    for j in range(3):
-        g2[(j + 1) % 3, j] = 1
+    if N == 3:
+        w = np.exp(2j * math.pi * k / 3)
+        g1 = np.diag([1, w, w * w]).astype(np.complex128)
+    else:
+        w = np.exp(2j * math.pi * k / N)
+        g1 = np.diag([w ** j for j in range(N)]).astype(np.complex128)
+    g2 = np.zeros((N, N), dtype=np.complex128)
+    for j in range(N):
+        g2[(j + 1) % N, j] = 1
+    if N % 2 == 0:
+        for g in (g1, g2):
+            d = np.linalg.det(g)
+            g *= np.exp(-1j * np.angle(d) / N)
     return g1, g2
 
 
-def twist_eater(L, k: int = 1) -> np.ndarray:
+def twist_eater(L, k: int = 1, N: int = 3) -> np.ndarray:
     """A field whose twisted plaquettes all equal their centre factor (zero twisted action).
 
     U_0(n) = Gamma_1 where x0 = 0, U_1(n) = Gamma_2 where x1 = 0, every other link
@@ -134,9 +176,9 @@ def twist_eater(L, k: int = 1) -> np.ndarray:
     x0 = x1 = 0 and P = 1 elsewhere (twist in the (0,1) plane, corner at the origin).
     """
     L0, L1, L2, L3 = (int(x) for x in L)
-    g1, g2 = twist_matrices(k)
-    U = np.zeros((L3, L2, L1, L0, 4, 3, 3), dtype=np.complex128)
-    U[...] = np.eye(3)
+    g1, g2 = twist_matrices(k, N)
+    U = np.zeros((L3, L2, L1, L0, 4, N, N), dtype=np.complex128)
+    U[...] = np.eye(N)
     U[:, :, :, 0, 0] = g1
     U[:, :, 0, :, 1] = g2
     return U
