@@ -183,6 +183,33 @@ tgf_status tgf_flow(int prec, const tgf_lattice *lat, int ncfg, void *w, void *w
 /* Number of records tgf_flow writes for one configuration (host arithmetic only). */
 tgf_status tgf_flow_records(double eps, double t_end, int measure_every, int *n_records);
 
+/* ---- SU(N) forms (FP64; Sec. 1, Sec. 3.1 with N colours, Sec. 5) ---------------------------- */
+
+/* The paper defines the coupling for SU(N) on the l x l x (Nl) x (Nl) box with the twist
+ * exp(2 pi i k / N) and gives numbers for N = 3; these calls run the same flow and measurement
+ * for N = 2, 3, 4 in FP64: Z = -P_ta(U Sigma) with the 1/N trace, Luscher's RK3 as in tgf_stage,
+ * exp(X) by its Taylor series after scaling X by 2^-s to ||X||_F <= 1/2 and squaring back, the
+ * twisted clover and plaquette as in tgf_measure with the twist n_{mu nu} taken mod N and
+ * P = (1/(6V)) sum_n sum_{mu<nu} (1/N) Re Tr[Z* P_{mu nu}].  Canonical buffers hold V x 4 x N x N
+ * complex doubles per configuration ([x3][x2][x1][x0][mu][row][col][re,im]); device storage is
+ * N^2 double2 planes per direction of Vp sites (Vp = V rounded up to 32), the accumulator N^2
+ * reals per link.  Errors: TGF_EINVAL for N outside 2..4 and as for the SU(3) calls. */
+tgf_status tgf_sun_links_bytes(int N, const tgf_lattice *lat, int ncfg, size_t *bytes);
+tgf_status tgf_sun_accum_bytes(int N, const tgf_lattice *lat, int ncfg, size_t *bytes);
+/* 4 doubles per 128-site block of every configuration, rounded up to 256 bytes */
+tgf_status tgf_sun_scratch_bytes(int N, const tgf_lattice *lat, int ncfg, size_t *bytes);
+tgf_status tgf_sun_pack(int N, const tgf_lattice *lat, int ncfg, const double *canon_dev, void *links, void *stream);
+tgf_status tgf_sun_unpack(int N, const tgf_lattice *lat, int ncfg, const void *links, double *canon_dev,
+                          void *stream);
+/* One RK3 stage s = 1, 2, 3 of size eps for every link (the SU(N) counterpart of tgf_stage). */
+tgf_status tgf_sun_stage(int N, const tgf_lattice *lat, int ncfg, const void *w_in, void *w_out, void *accum,
+                         int stage, double eps, void *stream);
+/* {t, E, Q, P, S} of every configuration into obs_dev[c * obs_stride + rec] (tgf_measure for SU(N);
+ * flags: TGF_CLOVER_TRACELESS subtracts tr(G)/N). */
+tgf_status tgf_sun_measure(int N, const tgf_lattice *lat, int ncfg, const void *links, double *scratch,
+                           size_t scratch_bytes, tgf_obs *obs_dev, size_t obs_stride, int rec, double t,
+                           unsigned flags, void *stream);
+
 /* ---- ensemble generation (Sec. 3.1) ------------------------------------------------------ */
 
 /* n_hybrid hybrid Monte Carlo sweeps of every configuration of `links` (TGF_FP64 storage), in

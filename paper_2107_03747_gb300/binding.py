@@ -63,6 +63,13 @@ _SIGS = {
     "tgf_slice_correlator": [C.POINTER(C.c_double), _SZ, C.POINTER(C.c_double), C.c_int, C.c_int,
                              C.POINTER(C.c_double), C.POINTER(C.c_int)],
     "tgf_measure_noalloc": [C.c_int, _LATP, C.c_int, _P, _P, _SZ, C.c_int, C.c_double, C.c_uint, _P],
+    "tgf_sun_links_bytes": [C.c_int, _LATP, C.c_int, C.POINTER(_SZ)],
+    "tgf_sun_accum_bytes": [C.c_int, _LATP, C.c_int, C.POINTER(_SZ)],
+    "tgf_sun_scratch_bytes": [C.c_int, _LATP, C.c_int, C.POINTER(_SZ)],
+    "tgf_sun_pack": [C.c_int, _LATP, C.c_int, _P, _P, _P],
+    "tgf_sun_unpack": [C.c_int, _LATP, C.c_int, _P, _P, _P],
+    "tgf_sun_stage": [C.c_int, _LATP, C.c_int, _P, _P, _P, C.c_int, C.c_double, _P],
+    "tgf_sun_measure": [C.c_int, _LATP, C.c_int, _P, _P, _SZ, _P, _SZ, C.c_int, C.c_double, C.c_uint, _P],
     "tgf_mc_sweeps": [C.c_int, _LATP, C.c_int, _P, C.c_double, C.c_int, C.c_int, C.c_ulonglong, C.c_ulonglong, _P],
     "tgf_norm": [C.c_double, C.c_int, C.c_int, C.POINTER(C.c_double)],
     "tgf_fma_peak": [C.c_int, _P, C.c_int, C.c_int, C.POINTER(C.c_double), _P],
@@ -244,6 +251,69 @@ def tgf_mc_sweeps(prec, lat, links, beta, n_hybrid, n_or, seed, first_sweep, str
     """n_hybrid hybrid sweeps (1 heat-bath + n_or over-relaxation each) of FP64 `links`, in place."""
     _check(_lib.tgf_mc_sweeps(prec, lat, len(lat), _ptr(links), float(beta), int(n_hybrid), int(n_or),
                               int(seed) & 0xFFFFFFFFFFFFFFFF, int(first_sweep), _stream(stream)))
+
+
+def _sun_size(fn, N, lat) -> int:
+    n = _SZ()
+    _check(fn(N, lat, len(lat), C.byref(n)))
+    return n.value
+
+
+class SunBatch:
+    """SU(N) configurations (FP64) with their device buffers: links, the ping-pong buffer, X, scratch."""
+
+    def __init__(self, N, Ls, twists=None, device="cuda"):
+        import torch
+
+        self.N, self.Ls, self.device = N, [tuple(L) for L in Ls], device
+        self.lat = lattices(self.Ls, twists)
+        nb = _sun_size(_lib.tgf_sun_links_bytes, N, self.lat)
+        self.links = torch.empty(nb, dtype=torch.uint8, device=device)
+        self.links_tmp = torch.empty(nb, dtype=torch.uint8, device=device)
+        self.accum = torch.empty(_sun_size(_lib.tgf_sun_accum_bytes, N, self.lat), dtype=torch.uint8, device=device)
+        self.scratch = torch.empty(_sun_size(_lib.tgf_sun_scratch_bytes, N, self.lat), dtype=torch.uint8, device=device)
+
+    def set_links(self, fields, stream=None):
+        import torch
+
+        flat = np.concatenate([np.ascontiguousarray(f).view(np.float64).reshape(-1) for f in fields])
+        canon = torch.from_numpy(flat).to(self.device)
+        _check(_lib.tgf_sun_pack(self.N, self.lat, len(self.lat), _ptr(canon), _ptr(self.links), _stream(stream)))
+        return canon
+
+    def get_links(self, stream=None):
+        import torch
+
+        N = self.N
+        n = sum(L[0] * L[1] * L[2] * L[3] * 4 * N * N * 2 for L in self.Ls)
+        canon = torch.empty(n, dtype=torch.float64, device=self.device)
+        _check(_lib.tgf_sun_unpack(N, self.lat, len(self.lat), _ptr(self.links), _ptr(canon), _stream(stream)))
+        flat = canon.cpu().numpy()
+        out, off = [], 0
+        for L in self.Ls:
+            m = L[0] * L[1] * L[2] * L[3] * 4 * N * N * 2
+            out.append(flat[off:off + m].view(np.complex128).reshape(L[3], L[2], L[1], L[0], 4, N, N))
+            off += m
+        return out
+
+    def stage(self, stage, eps, stream=None):
+        _check(_lib.tgf_sun_stage(self.N, self.lat, len(self.lat), _ptr(self.links), _ptr(self.links_tmp),
+                                  _ptr(self.accum), stage, eps, _stream(stream)))
+        self.links, self.links_tmp = self.links_tmp, self.links
+
+    def step(self, eps, stream=None):
+        for s in (1, 2, 3):
+            self.stage(s, eps, stream)
+
+    def measure(self, t=0.0, flags=0, stream=None):
+        """{t, E, Q, P, S} per configuration as an (ncfg, 5) numpy array."""
+        import torch
+
+        n = len(self.lat)
+        obs = torch.zeros(n * 5, dtype=torch.float64, device=self.device)
+        _check(_lib.tgf_sun_measure(self.N, self.lat, n, _ptr(self.links), _ptr(self.scratch),
+                                    self.scratch.numel(), _ptr(obs), 1, 0, t, flags, _stream(stream)))
+        return obs.cpu().numpy().reshape(n, 5)
 
 
 def tgf_norm(c, Lt, N=3) -> float:

@@ -406,6 +406,148 @@ tgf_status tgf_measure(int prec, const tgf_lattice* lat, int ncfg, const void* l
                            (cudaStream_t)stream);
 }
 
+// ---- SU(N) forms (FP64) -------------------------------------------------------------------
+
+namespace {
+
+constexpr int kSunMeasureSites = 128;
+
+tgf_status check_n(int N) {
+    if (N < 2 || N > 4) return fail(TGF_EINVAL, "N = %d outside the supported 2..4", N);
+    return TGF_OK;
+}
+
+// per-configuration offsets in doubles: links (4 N^2 complex planes of Vp), X (4 N^2 reals of Vp),
+// canonical (V x 4 x N^2 complex); blocks of `spb` sites
+Batch make_sun_batch(int N, const tgf_lattice* lat, int ncfg, int spb) {
+    Batch B;
+    B.ncfg = ncfg;
+    int blk = 0;
+    int64_t w = 0, x = 0, cc = 0;
+    for (int c = 0; c < ncfg; ++c) {
+        CfgDesc& d = B.c[c];
+        for (int mu = 0; mu < 4; ++mu) d.L[mu] = lat[c].L[mu];
+        d.st[0] = 1;
+        for (int mu = 1; mu < 4; ++mu) d.st[mu] = d.st[mu - 1] * d.L[mu - 1];
+        d.V = (int)sites(lat[c]);
+        d.Vp = (int)padded(d.V);
+        d.blk0 = blk;
+        d.rec = 0;
+        d.w_off = w;
+        d.x_off = x;
+        d.m_off = cc;
+        d.o_off = 0;
+        d.h = 0.0;
+        const int pairs[6][2] = {{0, 1}, {0, 2}, {0, 3}, {1, 2}, {1, 3}, {2, 3}};
+        std::memset(d.tw, 0, 16);
+        for (int i = 0; i < 6; ++i) {
+            const int k = ((lat[c].twist[i] % N) + N) % N;
+            d.tw[pairs[i][0] * 4 + pairs[i][1]] = (int8_t)k;
+            d.tw[pairs[i][1] * 4 + pairs[i][0]] = (int8_t)((N - k) % N);
+        }
+        w += (int64_t)4 * N * N * 2 * d.Vp;
+        x += (int64_t)4 * N * N * d.Vp;
+        cc += (int64_t)d.V * 4 * N * N * 2;
+        blk += (d.V + spb - 1) / spb;
+    }
+    B.nblk = blk;
+    return B;
+}
+
+size_t sun_scratch(const tgf_lattice* lat, int ncfg) {
+    size_t nb = 0;
+    for (int c = 0; c < ncfg; ++c) nb += (size_t)((sites(lat[c]) + kSunMeasureSites - 1) / kSunMeasureSites);
+    return (nb * 4 * sizeof(double) + 255) / 256 * 256;
+}
+
+}  // namespace
+
+tgf_status tgf_sun_links_bytes(int N, const tgf_lattice* lat, int ncfg, size_t* bytes) {
+    tgf_status s;
+    if ((s = check_n(N)) || (s = check_lat(lat, ncfg))) return s;
+    if (!bytes) return fail(TGF_EINVAL, "bytes is NULL");
+    size_t b = 0;
+    for (int c = 0; c < ncfg; ++c) b += (size_t)4 * N * N * 16 * (size_t)padded(sites(lat[c]));
+    *bytes = b;
+    return TGF_OK;
+}
+
+tgf_status tgf_sun_accum_bytes(int N, const tgf_lattice* lat, int ncfg, size_t* bytes) {
+    tgf_status s;
+    if ((s = check_n(N)) || (s = check_lat(lat, ncfg))) return s;
+    if (!bytes) return fail(TGF_EINVAL, "bytes is NULL");
+    size_t b = 0;
+    for (int c = 0; c < ncfg; ++c) b += (size_t)4 * N * N * 8 * (size_t)padded(sites(lat[c]));
+    *bytes = b;
+    return TGF_OK;
+}
+
+tgf_status tgf_sun_scratch_bytes(int N, const tgf_lattice* lat, int ncfg, size_t* bytes) {
+    tgf_status s;
+    if ((s = check_n(N)) || (s = check_lat(lat, ncfg))) return s;
+    if (!bytes) return fail(TGF_EINVAL, "bytes is NULL");
+    *bytes = sun_scratch(lat, ncfg);
+    return TGF_OK;
+}
+
+tgf_status tgf_sun_pack(int N, const tgf_lattice* lat, int ncfg, const double* canon_dev, void* links, void* stream) {
+    tgf_status s;
+    if ((s = check_n(N)) || (s = check_lat(lat, ncfg)) || (s = check_ptr(canon_dev, "canon_dev")) ||
+        (s = check_ptr(links, "links")))
+        return s;
+    Batch B = make_sun_batch(N, lat, ncfg, 128);
+    launch_sun_layout(N, true, B, const_cast<double*>(canon_dev), static_cast<double*>(links), (cudaStream_t)stream);
+    return last_launch("SU(N) pack");
+}
+
+tgf_status tgf_sun_unpack(int N, const tgf_lattice* lat, int ncfg, const void* links, double* canon_dev, void* stream) {
+    tgf_status s;
+    if ((s = check_n(N)) || (s = check_lat(lat, ncfg)) || (s = check_ptr(canon_dev, "canon_dev")) ||
+        (s = check_ptr(links, "links")))
+        return s;
+    Batch B = make_sun_batch(N, lat, ncfg, 128);
+    launch_sun_layout(N, false, B, canon_dev, const_cast<double*>(static_cast<const double*>(links)),
+                      (cudaStream_t)stream);
+    return last_launch("SU(N) unpack");
+}
+
+tgf_status tgf_sun_stage(int N, const tgf_lattice* lat, int ncfg, const void* w_in, void* w_out, void* accum, int stage,
+                         double eps, void* stream) {
+    tgf_status s;
+    if ((s = check_n(N)) || (s = check_lat(lat, ncfg)) || (s = check_ptr(w_in, "w_in")) ||
+        (s = check_ptr(w_out, "w_out")) || (s = check_ptr(accum, "accum")))
+        return s;
+    if (stage < 1 || stage > 3) return fail(TGF_EINVAL, "stage %d outside 1..3", stage);
+    if (!(std::isfinite(eps)) || eps == 0.0) return fail(TGF_EINVAL, "eps = %g must be finite and non-zero", eps);
+    if (w_in == w_out) return fail(TGF_EINVAL, "w_in and w_out must be distinct buffers");
+    Batch B = make_sun_batch(N, lat, ncfg, 32);
+    for (int i = 0; i < ncfg; ++i) B.c[i].h = eps;
+    launch_sun_stage(N, stage, B, static_cast<const double*>(w_in), static_cast<double*>(w_out),
+                     static_cast<double*>(accum), (cudaStream_t)stream);
+    return last_launch("SU(N) stage");
+}
+
+tgf_status tgf_sun_measure(int N, const tgf_lattice* lat, int ncfg, const void* links, double* scratch,
+                           size_t scratch_bytes, tgf_obs* obs_dev, size_t obs_stride, int rec, double t, unsigned flags,
+                           void* stream) {
+    tgf_status s;
+    if ((s = check_n(N)) || (s = check_lat(lat, ncfg)) || (s = check_ptr(links, "links")) ||
+        (s = check_ptr(scratch, "scratch")) || (s = check_ptr(obs_dev, "obs_dev")))
+        return s;
+    if (scratch_bytes < sun_scratch(lat, ncfg))
+        return fail(TGF_EINVAL, "scratch of %zu bytes too small (need %zu)", scratch_bytes, sun_scratch(lat, ncfg));
+    if (rec < 0 || (ncfg > 1 && (size_t)rec >= obs_stride))
+        return fail(TGF_EINVAL, "record %d outside the stride %zu", rec, obs_stride);
+    Batch B = make_sun_batch(N, lat, ncfg, kSunMeasureSites);
+    for (int i = 0; i < ncfg; ++i) {
+        B.c[i].h = t;
+        B.c[i].o_off = (int64_t)i * (int64_t)obs_stride + rec;
+    }
+    launch_sun_measure(N, B, B, static_cast<const double*>(links), scratch, reinterpret_cast<double*>(obs_dev),
+                       (flags & TGF_CLOVER_TRACELESS) ? 1 : 0, (cudaStream_t)stream);
+    return last_launch("SU(N) measure");
+}
+
 tgf_status tgf_mc_sweeps(int prec, const tgf_lattice* lat, int ncfg, void* links, double beta, int n_hybrid, int n_or,
                          unsigned long long seed, unsigned long long first_sweep, void* stream) {
     tgf_status s;

@@ -211,6 +211,14 @@ void launch_reduce(const Batch& B, const double* partial, double* obs, cudaStrea
 void launch_slice_charge(int prec, unsigned flags, const Batch& B, const void* clov, int dir, double* q, int q_stride,
                          cudaStream_t st);
 void launch_pack(int prec, const Batch& B, const double* canon, void* w, cudaStream_t st);
+// SU(N) forms (N = 2, 3, 4; FP64): one RK3 stage (batch of 32-site blocks), the measurement
+// (measure batch of 128-site blocks with o_off / h set; partial holds 4 doubles per block), and
+// canonical <-> storage layout (batch of 128-site blocks, m_off = canonical offset in doubles)
+void launch_sun_stage(int N, int stage, const Batch& B, const double* w_in, double* w_out, double* acc,
+                      cudaStream_t st);
+void launch_sun_measure(int N, const Batch& Bm, const Batch& Br, const double* w, double* partial, double* obs,
+                        int traceless, cudaStream_t st);
+void launch_sun_layout(int N, bool to_storage, const Batch& B, double* canon, double* w, cudaStream_t st);
 // one checkerboard pass of the Monte Carlo update (FP64 storage): links of direction mu on the
 // sites of the given parity; heat-bath (overrelax = 0) or over-relaxation; the batch has
 // ceil(V / 256) blocks of 128 threads per configuration
