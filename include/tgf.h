@@ -58,7 +58,8 @@ typedef enum {
     TGF_EINVAL = 1,   /* bad argument: extents, twist, sizes, pointers, eps, t_end   */
     TGF_ECUDA = 3,    /* a CUDA runtime call failed (message in tgf_last_error)      */
     TGF_EKERNEL = 4,  /* reserved: kernels report no status (non-finite inputs give NaN records) */
-    TGF_ESTATE = 6    /* no configuration survived the |Q| < 1/2 cut                  */
+    TGF_ESTATE = 6,   /* no configuration survived the |Q| < 1/2 cut                  */
+    TGF_EIO = 7       /* checkpoint file missing, unreadable, truncated or corrupted  */
 } tgf_status;
 
 typedef enum {
@@ -231,6 +232,28 @@ tgf_status tgf_sun_measure(int N, const tgf_lattice *lat, int ncfg, const void *
  * counts.  Enqueues 8 (1 + n_or) n_hybrid launches on `stream`. */
 tgf_status tgf_mc_sweeps(int prec, const tgf_lattice *lat, int ncfg, void *links, double beta, int n_hybrid,
                          int n_or, unsigned long long seed, unsigned long long first_sweep, void *stream);
+
+/* ---- checkpoints --------------------------------------------------------------------------- */
+
+/* Between RK3 steps the state of a flow is the field alone (X is rebuilt by stage 1), so a
+ * checkpoint is the links in canonical FP64 with the flow time, the step count and a seed.
+ * File (little-endian): 48-byte header {"TGFCKPT1", u32 version = 1, u32 ncfg, i32 precision the
+ * links were stored in, i32 0, f64 t, i64 step, u64 seed}, then per configuration i32 L[4] and
+ * i32 twist[6], then the canonical fields of all configurations (V x 72 doubles each), then the
+ * CRC-32 (IEEE 802.3, as zlib's crc32) of everything before it.
+ * tgf_save downloads `links` through the caller's staging buffer (as tgf_download; synchronises
+ * `stream`) and writes `path`.  tgf_load reads and checks the whole file on the host first (magic,
+ * version, CRC, size, and extents and twist mod 3 equal to `lat`), then uploads through the
+ * staging buffer into `links` (any precision; FP32 forms round) and returns t, step and seed
+ * (each pointer may be NULL).  Errors: TGF_EIO for a missing, unreadable, truncated or
+ * corrupted file, TGF_EINVAL for a lattice mismatch or bad arguments; nothing is written to the
+ * device unless the file passes every check. */
+tgf_status tgf_save(const char *path, int prec, const tgf_lattice *lat, int ncfg, const void *links, double *staging_dev,
+                    size_t staging_bytes, double t, long long step, unsigned long long seed, void *stream);
+tgf_status tgf_load(const char *path, int prec, const tgf_lattice *lat, int ncfg, void *links, double *staging_dev,
+                    size_t staging_bytes, double *t, long long *step, unsigned long long *seed, void *stream);
+/* CRC-32 of n bytes (the checkpoint checksum; host only). */
+unsigned int tgf_crc32(const void *data, size_t n);
 
 /* ---- coupling (host only) ----------------------------------------------------------------- */
 

@@ -16,7 +16,7 @@ PKG = os.path.dirname(os.path.abspath(__file__))
 # TGF_LIB_PATH selects another build of the same library (kernel-variant sweeps of the tuner)
 LIB_PATH = os.environ.get("TGF_LIB_PATH", os.path.join(PKG, "libtgf.so"))
 
-TGF_OK, TGF_EINVAL, TGF_ECUDA, TGF_EKERNEL, TGF_ESTATE = 0, 1, 3, 4, 6
+TGF_OK, TGF_EINVAL, TGF_ECUDA, TGF_EKERNEL, TGF_ESTATE, TGF_EIO = 0, 1, 3, 4, 6, 7
 TGF_FP64, TGF_FP32, TGF_FP32_R12 = 0, 1, 2
 TGF_CLOVER_TRACELESS = 1
 TGF_NO_GRAPH = 2
@@ -71,6 +71,9 @@ _SIGS = {
     "tgf_sun_stage": [C.c_int, _LATP, C.c_int, _P, _P, _P, C.c_int, C.c_double, _P],
     "tgf_sun_measure": [C.c_int, _LATP, C.c_int, _P, _P, _SZ, _P, _SZ, C.c_int, C.c_double, C.c_uint, _P],
     "tgf_mc_sweeps": [C.c_int, _LATP, C.c_int, _P, C.c_double, C.c_int, C.c_int, C.c_ulonglong, C.c_ulonglong, _P],
+    "tgf_save": [C.c_char_p, C.c_int, _LATP, C.c_int, _P, _P, _SZ, C.c_double, C.c_longlong, C.c_ulonglong, _P],
+    "tgf_load": [C.c_char_p, C.c_int, _LATP, C.c_int, _P, _P, _SZ, C.POINTER(C.c_double), C.POINTER(C.c_longlong),
+                 C.POINTER(C.c_ulonglong), _P],
     "tgf_norm": [C.c_double, C.c_int, C.c_int, C.POINTER(C.c_double)],
     "tgf_fma_peak": [C.c_int, _P, C.c_int, C.c_int, C.POINTER(C.c_double), _P],
     "tgf_lambda": [C.c_double, C.c_int, C.c_double, C.POINTER(C.c_double), C.POINTER(C.c_double), C.c_int,
@@ -80,6 +83,8 @@ for _name, _args in _SIGS.items():
     _f = getattr(_lib, _name)
     _f.argtypes = _args
     _f.restype = C.c_int
+_lib.tgf_crc32.restype = C.c_uint
+_lib.tgf_crc32.argtypes = [C.c_void_p, C.c_size_t]
 _lib.tgf_last_error.restype = C.c_char_p
 _lib.tgf_last_error.argtypes = []
 _lib.tgf_status_string.restype = C.c_char_p
@@ -87,7 +92,7 @@ _lib.tgf_status_string.argtypes = [C.c_int]
 _lib.tgf_version.restype = C.c_char_p
 _lib.tgf_version.argtypes = []
 
-EXPORTED = sorted(list(_SIGS) + ["tgf_last_error", "tgf_status_string", "tgf_version"])
+EXPORTED = sorted(list(_SIGS) + ["tgf_last_error", "tgf_status_string", "tgf_version", "tgf_crc32"])
 
 
 def _check(status: int):
@@ -314,6 +319,26 @@ class SunBatch:
         _check(_lib.tgf_sun_measure(self.N, self.lat, n, _ptr(self.links), _ptr(self.scratch),
                                     self.scratch.numel(), _ptr(obs), 1, 0, t, flags, _stream(stream)))
         return obs.cpu().numpy().reshape(n, 5)
+
+
+def tgf_crc32(data: bytes) -> int:
+    return int(_lib.tgf_crc32(data, len(data)))
+
+
+def tgf_save(path, prec, lat, links, staging, t, step, seed, stream=None):
+    """Checkpoint `links` (canonical FP64 + t, step, seed, CRC-32) to `path`; synchronises `stream`."""
+    _check(_lib.tgf_save(str(path).encode(), prec, lat, len(lat), _ptr(links), _ptr(staging),
+                         staging.numel() * staging.element_size(), float(t), int(step),
+                         int(seed) & 0xFFFFFFFFFFFFFFFF, _stream(stream)))
+
+
+def tgf_load(path, prec, lat, links, staging, stream=None):
+    """Load a checkpoint into `links`; returns (t, step, seed)."""
+    t, step, seed = C.c_double(), C.c_longlong(), C.c_ulonglong()
+    _check(_lib.tgf_load(str(path).encode(), prec, lat, len(lat), _ptr(links), _ptr(staging),
+                         staging.numel() * staging.element_size(), C.byref(t), C.byref(step), C.byref(seed),
+                         _stream(stream)))
+    return t.value, step.value, seed.value
 
 
 def tgf_norm(c, Lt, N=3) -> float:

@@ -260,6 +260,7 @@ const char* tgf_status_string(int status) {
         case TGF_ECUDA: return "CUDA error";
         case TGF_EKERNEL: return "kernel error";
         case TGF_ESTATE: return "no configuration kept";
+        case TGF_EIO: return "checkpoint file error";
         default: return "unknown status";
     }
 }
@@ -404,6 +405,135 @@ tgf_status tgf_measure(int prec, const tgf_lattice* lat, int ncfg, const void* l
     std::vector<double> ts(ncfg, t);
     return enqueue_measure(prec, flags, lat, Ly, which, recs, ts, obs_stride, links, scratch, obs_dev,
                            (cudaStream_t)stream);
+}
+
+// ---- checkpoints ---------------------------------------------------------------------------
+
+namespace {
+
+// CRC-32 of IEEE 802.3 (reflected polynomial 0xEDB88320, initial value and final xor 0xFFFFFFFF)
+uint32_t crc32_update(uint32_t crc, const unsigned char* p, size_t n) {
+    static uint32_t table[256];
+    static std::once_flag once;
+    std::call_once(once, [] {
+        for (uint32_t i = 0; i < 256; ++i) {
+            uint32_t c = i;
+            for (int k = 0; k < 8; ++k) c = (c & 1u) ? 0xEDB88320u ^ (c >> 1) : c >> 1;
+            table[i] = c;
+        }
+    });
+    for (size_t i = 0; i < n; ++i) crc = table[(crc ^ p[i]) & 0xFFu] ^ (crc >> 8);
+    return crc;
+}
+
+constexpr char kMagic[8] = {'T', 'G', 'F', 'C', 'K', 'P', 'T', '1'};
+
+struct CkptHeader {
+    char magic[8];
+    uint32_t version;
+    uint32_t ncfg;
+    int32_t precision;
+    int32_t reserved;
+    double t;
+    int64_t step;
+    uint64_t seed;
+};
+static_assert(sizeof(CkptHeader) == 48, "checkpoint header layout");
+
+struct CkptLattice {
+    int32_t L[4];
+    int32_t twist[6];
+};
+
+}  // namespace
+
+uint32_t tgf_crc32(const void* data, size_t n) {
+    return crc32_update(0xFFFFFFFFu, static_cast<const unsigned char*>(data), n) ^ 0xFFFFFFFFu;
+}
+
+tgf_status tgf_save(const char* path, int prec, const tgf_lattice* lat, int ncfg, const void* links, double* staging_dev,
+                    size_t staging_bytes, double t, long long step, unsigned long long seed, void* stream) {
+    tgf_status s;
+    if (!path) return fail(TGF_EINVAL, "path is NULL");
+    if ((s = check_prec(prec)) || (s = check_lat(lat, ncfg)) || (s = check_ptr(links, "links"))) return s;
+    size_t total = 0;
+    for (int c = 0; c < ncfg; ++c) total += (size_t)sites(lat[c]) * 72;
+    std::vector<double> canon(total);
+    if ((s = tgf_download(prec, lat, ncfg, links, staging_dev, staging_bytes, canon.data(), stream))) return s;
+    CkptHeader h{};
+    std::memcpy(h.magic, kMagic, 8);
+    h.version = 1;
+    h.ncfg = (uint32_t)ncfg;
+    h.precision = prec;
+    h.t = t;
+    h.step = (int64_t)step;
+    h.seed = (uint64_t)seed;
+    std::vector<CkptLattice> lt(ncfg);
+    for (int c = 0; c < ncfg; ++c) {
+        for (int m = 0; m < 4; ++m) lt[c].L[m] = lat[c].L[m];
+        for (int i = 0; i < 6; ++i) lt[c].twist[i] = lat[c].twist[i];
+    }
+    uint32_t crc = 0xFFFFFFFFu;
+    crc = crc32_update(crc, reinterpret_cast<const unsigned char*>(&h), sizeof h);
+    crc = crc32_update(crc, reinterpret_cast<const unsigned char*>(lt.data()), lt.size() * sizeof(CkptLattice));
+    crc = crc32_update(crc, reinterpret_cast<const unsigned char*>(canon.data()), canon.size() * sizeof(double));
+    crc ^= 0xFFFFFFFFu;
+    FILE* f = std::fopen(path, "wb");
+    if (!f) return fail(TGF_EIO, "cannot open %s for writing", path);
+    bool ok = std::fwrite(&h, sizeof h, 1, f) == 1 &&
+              std::fwrite(lt.data(), sizeof(CkptLattice), lt.size(), f) == lt.size() &&
+              std::fwrite(canon.data(), sizeof(double), canon.size(), f) == canon.size() &&
+              std::fwrite(&crc, sizeof crc, 1, f) == 1;
+    ok = (std::fclose(f) == 0) && ok;
+    if (!ok) return fail(TGF_EIO, "write to %s failed", path);
+    return TGF_OK;
+}
+
+tgf_status tgf_load(const char* path, int prec, const tgf_lattice* lat, int ncfg, void* links, double* staging_dev,
+                    size_t staging_bytes, double* t, long long* step, unsigned long long* seed, void* stream) {
+    tgf_status s;
+    if (!path) return fail(TGF_EINVAL, "path is NULL");
+    if ((s = check_prec(prec)) || (s = check_lat(lat, ncfg)) || (s = check_ptr(links, "links"))) return s;
+    FILE* f = std::fopen(path, "rb");
+    if (!f) return fail(TGF_EIO, "cannot open %s", path);
+    std::vector<unsigned char> buf;
+    unsigned char chunk[1 << 16];
+    size_t n;
+    while ((n = std::fread(chunk, 1, sizeof chunk, f)) > 0) buf.insert(buf.end(), chunk, chunk + n);
+    std::fclose(f);
+    if (buf.size() < sizeof(CkptHeader) + sizeof(uint32_t)) return fail(TGF_EIO, "%s: too short for a checkpoint", path);
+    CkptHeader h;
+    std::memcpy(&h, buf.data(), sizeof h);
+    if (std::memcmp(h.magic, kMagic, 8) != 0 || h.version != 1) return fail(TGF_EIO, "%s: not a libtgf checkpoint", path);
+    uint32_t stored;
+    std::memcpy(&stored, buf.data() + buf.size() - sizeof stored, sizeof stored);
+    if (tgf_crc32(buf.data(), buf.size() - sizeof stored) != stored) return fail(TGF_EIO, "%s: CRC mismatch", path);
+    if ((int)h.ncfg != ncfg) return fail(TGF_EINVAL, "%s holds %u configurations, the call %d", path, h.ncfg, ncfg);
+    const unsigned char* p = buf.data() + sizeof h;
+    size_t total = 0;
+    for (int c = 0; c < ncfg; ++c) {
+        CkptLattice l;
+        std::memcpy(&l, p + c * sizeof l, sizeof l);
+        for (int m = 0; m < 4; ++m)
+            if (l.L[m] != lat[c].L[m])
+                return fail(TGF_EINVAL, "%s: configuration %d has L[%d] = %d, the call %d", path, c, m, l.L[m],
+                            lat[c].L[m]);
+        for (int i = 0; i < 6; ++i)
+            if (((l.twist[i] - lat[c].twist[i]) % 3 + 3) % 3 != 0)
+                return fail(TGF_EINVAL, "%s: configuration %d has another twist", path, c);
+        total += (size_t)sites(lat[c]) * 72;
+    }
+    const size_t data_off = sizeof h + (size_t)ncfg * sizeof(CkptLattice);
+    if (buf.size() != data_off + total * sizeof(double) + sizeof(uint32_t))
+        return fail(TGF_EIO, "%s: size does not match its lattices", path);
+    std::vector<double> canon(total);
+    std::memcpy(canon.data(), buf.data() + data_off, total * sizeof(double));
+    if ((s = tgf_upload(prec, lat, ncfg, canon.data(), staging_dev, staging_bytes, links, stream))) return s;
+    TGF_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+    if (t) *t = h.t;
+    if (step) *step = (long long)h.step;
+    if (seed) *seed = (unsigned long long)h.seed;
+    return TGF_OK;
 }
 
 // ---- SU(N) forms (FP64) -------------------------------------------------------------------

@@ -154,3 +154,60 @@ def test_mc_bad_arguments_are_rejected_before_device_work(lib, bad):
     s = lib._lib.tgf_mc_sweeps(prec, lat, 1, ptr, beta, nh, 1, 0, 0, None)
     assert s == lib.TGF_EINVAL
     assert len(lib._lib.tgf_last_error()) > 0
+
+
+# ---- checkpoints (host side: the file is checked completely before any device work) ----------------
+
+def test_crc32_is_the_ieee_checksum(lib):
+    import zlib
+
+    assert lib.tgf_crc32(b"123456789") == 0xCBF43926  # the CRC-32 check value of the standard
+    rng = np.random.default_rng(0)
+    for n in (0, 1, 7, 1000, 65537):
+        b = rng.integers(0, 256, n, dtype=np.uint8).tobytes()
+        assert lib.tgf_crc32(b) == zlib.crc32(b)
+
+
+def _checkpoint_bytes(Ls, twists, fields, t=0.5, step=50, seed=7, prec=0):
+    """A checkpoint written from the format description alone (header, lattices, data, CRC-32)."""
+    import struct
+    import zlib
+
+    body = b"TGFCKPT1" + struct.pack("<IIiidqQ", 1, len(Ls), prec, 0, t, step, seed)
+    for L, tw in zip(Ls, twists):
+        body += struct.pack("<4i6i", *L, *tw)
+    for f in fields:
+        body += np.ascontiguousarray(f).view(np.float64).tobytes()
+    return body + struct.pack("<I", zlib.crc32(body))
+
+
+@pytest.mark.parametrize("bad", ["missing", "magic", "crc", "short", "ncfg", "extent", "twist"])
+def test_load_rejects_bad_files_before_device_work(lib, tmp_path, bad):
+    Ls = [(2, 2, 6, 6)]
+    tw = [(1, 0, 0, 0, 0, 0)]
+    f = np.zeros((6, 6, 2, 2, 4, 3, 3), dtype=np.complex128)
+    good = _checkpoint_bytes(Ls, tw, [f])
+    path = tmp_path / "ck.tgf"
+    lat = lib.lattices(Ls)
+    want = lib.TGF_EIO
+    if bad == "missing":
+        path = tmp_path / "none.tgf"
+    elif bad == "magic":
+        path.write_bytes(b"X" + good[1:])
+    elif bad == "crc":
+        path.write_bytes(good[:100] + bytes([good[100] ^ 1]) + good[101:])
+    elif bad == "short":
+        path.write_bytes(good[:40])
+    else:
+        path.write_bytes(good)
+        want = lib.TGF_EINVAL
+        if bad == "ncfg":
+            lat = lib.lattices(Ls * 2)
+        elif bad == "extent":
+            lat = lib.lattices([(2, 2, 6, 8)])
+        else:
+            lat = lib.lattices(Ls, [(2, 0, 0, 0, 0, 0)])
+    ptr = 1 << 20  # never dereferenced: every check above fails before the upload
+    s = lib._lib.tgf_load(str(path).encode(), 0, lat, len(lat), ptr, 2 * ptr, 1 << 20, None, None, None, None)
+    assert s == want
+    assert len(lib._lib.tgf_last_error()) > 0

@@ -406,3 +406,35 @@ def test_resumed_flow_is_bitwise_identical(tgf, prec):
     ra = oa.cpu().numpy()[0, : na[0]]
     rb = np.concatenate([ob1.cpu().numpy()[0, : nb1[0] - 1], ob2.cpu().numpy()[0, : nb2[0]]])
     assert np.array_equal(ra[:, 1:], rb[:, 1:])
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_checkpoint_resume_is_bitwise_identical(tgf, prec, tmp_path):
+    """tgf_save at t = 0.04, tgf_load into a fresh batch, flow on: the same field as one flow to t = 0.10.
+    The file is also parsed here from the format description (header, lattice, data, zlib CRC-32)."""
+    import struct
+    import zlib
+
+    import torch
+
+    L = (4, 4, 12, 12)
+    U = I.random_links(L, 97, 0.5)
+    a = load(tgf, [L], [U], prec)
+    a.flow(0.01, 0.10)
+    b = load(tgf, [L], [U], prec)
+    b.flow(0.01, 0.04)
+    staging = torch.empty(L[0] * L[1] * L[2] * L[3] * 72, dtype=torch.float64, device="cuda")
+    path = tmp_path / "mid.tgf"
+    tgf.tgf_save(path, b.prec, b.lat, b.links, staging, 0.04, 4, 1234)
+    raw = path.read_bytes()
+    assert zlib.crc32(raw[:-4]) == struct.unpack("<I", raw[-4:])[0]
+    magic, ver, ncfg, p, _, t, step, seed = struct.unpack("<8sIIiidqQ", raw[:48])
+    assert (magic, ver, ncfg, t, step, seed) == (b"TGFCKPT1", 1, 1, 0.04, 4, 1234)
+    assert struct.unpack("<4i6i", raw[48:88]) == (*L, 1, 0, 0, 0, 0, 0)
+    data = np.frombuffer(raw[88:-4], dtype=np.complex128).reshape(U.shape)
+    assert np.array_equal(data, b.get_links()[0])
+    c = tgf.FlowBatch([L], prec)
+    assert tgf.tgf_load(path, c.prec, c.lat, c.links, staging) == (0.04, 4, 1234)
+    assert np.array_equal(c.get_links()[0], b.get_links()[0])
+    c.flow(0.01, 0.06)
+    assert np.array_equal(a.get_links()[0], c.get_links()[0])
