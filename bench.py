@@ -305,11 +305,18 @@ def run_tgf(args):
         return lams
 
     reunit = args.reunit if prec != tgf.TGF_FP64 else 0
+    flags = 0
+    if args.tune:
+        # launch settings of tgf_flow timed on this workload (results are the same for all of them)
+        from paper_2107_03747_gb300 import tune
+
+        tgf.tgf_pack(prec, b.lat, canon_dev, b.links)
+        flags = tune.tune(b, eps=EPS, steps=4, measure_every=1, force=True)
 
     def step():
         tgf.tgf_pack(prec, b.lat, canon_dev, b.links)
         nrec = tgf.tgf_flow(prec, b.lat, b.links, b.links_tmp, b.accum, b.scratch, EPS, t_end, obs, cap, 1,
-                            reunit, 0)
+                            reunit, flags)
         obs_host.copy_(obs, non_blocking=True)
         stream.synchronize()
         return lam_of(obs_host, nrec), nrec
@@ -339,7 +346,7 @@ def run_tgf(args):
     def step_e2e():
         tgf.tgf_upload(prec, b.lat, canon_host, staging, b.links)
         nrec = tgf.tgf_flow(prec, b.lat, b.links, b.links_tmp, b.accum, b.scratch, EPS, t_end, obs, cap, 1,
-                            reunit, 0)
+                            reunit, flags)
         obs_host.copy_(obs, non_blocking=True)
         stream.synchronize()
         return lam_of(obs_host, nrec)
@@ -474,7 +481,9 @@ def run_tgf(args):
                        "site_steps_per_gpu": work, "link_bytes": link_bytes,
                        "l2": ("inputs larger than L2" if link_bytes > L2_BYTES else "inputs smaller than L2") +
                              f" ({link_bytes / 1e6:.0f} MB links, {canon_bytes / 1e6:.0f} MB canonical)",
-                       "parallelism": f"replicas x{ws}", "graph": True},
+                       "parallelism": f"replicas x{ws}", "graph": True,
+                       "launch_tuning": {"flags": flags, "grid_k": (flags >> 8) & 0xF,
+                                         "size_order": bool(flags & (1 << 12)), "tuned": bool(args.tune)}},
             "e2e": {"value": e2e_value, "unit": "site-steps/s", "h2d_bytes_per_step": canon_bytes,
                     "d2h_bytes_per_step": obs_host.numel() * 8, "ms_per_step": ms_e2e},
             "gpu_launches": launches_per_flow(members) * args.steps,
@@ -505,6 +514,8 @@ def main():
     ap.add_argument("--workload", default="l8x16", choices=sorted(WORKLOADS))
     ap.add_argument("--reunit", type=int, default=20, help="FP32 forms: re-project onto SU(3) every R steps")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison flow")
+    ap.add_argument("--no-tune", dest="tune", action="store_false",
+                    help="use the default launch settings instead of timing the candidates first")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle timing")
     ap.add_argument("--fp64-loop", action="store_true",
                     help="also time the ensemble as a loop of single-configuration FP64 flows")

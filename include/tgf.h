@@ -73,6 +73,13 @@ typedef enum {
 /* Flags of tgf_measure / tgf_flow. */
 #define TGF_CLOVER_TRACELESS 1u   /* subtract tr(G)/3 from the clover G (eq. gmunu has no projection) */
 #define TGF_NO_GRAPH 2u           /* tgf_flow: launch kernels directly instead of one CUDA graph      */
+/* Launch tuning of tgf_flow (results are bitwise the same for every setting; the tuner of the
+ * Python package times them per workload): TGF_TUNE_GRID(k), k = 1..15, launches the stage
+ * kernels as a persistent grid of k x (number of SMs) x (resident blocks per SM: 4 in FP32,
+ * 2 in FP64) that loops over the tiles, instead of one block per tile (k = 0);
+ * TGF_TUNE_SIZE_ORDER orders the configurations of each launch by size, largest first. */
+#define TGF_TUNE_GRID(k) (((unsigned)(k) & 0xFu) << 8)
+#define TGF_TUNE_SIZE_ORDER (1u << 12)
 
 typedef struct {
     int L[4];      /* extents, x0 fastest                                          */

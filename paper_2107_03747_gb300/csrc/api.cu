@@ -764,6 +764,15 @@ static tgf_status enqueue_flow(int prec, const tgf_lattice* lat, int ncfg, const
         maxT = std::max(maxT, total[c]);
     }
     std::vector<int> rec(ncfg, 0);
+    // tuning (flags): a persistent grid of k x SMs x resident blocks, configurations by size
+    int grid = 0;
+    if (const int k = (int)((flags >> 8) & 0xFu)) {
+        int dev = 0, sms = 0;
+        TGF_CUDA(cudaGetDevice(&dev));
+        TGF_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        grid = k * sms * (prec == TGF_FP64 ? 2 : 4);
+    }
+    const bool by_size = (flags & TGF_TUNE_SIZE_ORDER) != 0;
     void* cur = w;
     void* alt = w_tmp;
     SideBranch* sb = nullptr;
@@ -796,6 +805,8 @@ static tgf_status enqueue_flow(int prec, const tgf_lattice* lat, int ncfg, const
         }
         // every active configuration starts at step 0, so either all of them are measured now or none
         const int mode1 = mw.empty() ? 0 : 1;
+        if (by_size)
+            std::stable_sort(act.begin(), act.end(), [&](int a, int b) { return sites(lat[a]) > sites(lat[b]); });
         Batch B = make_batch(lat, Ly, act, 32);
         for (int k = 0; k < B.ncfg; ++k) {
             const int c = act[k];
@@ -803,7 +814,7 @@ static tgf_status enqueue_flow(int prec, const tgf_lattice* lat, int ncfg, const
         }
         const int ru = (prec != TGF_FP64 && reunit_every > 0 && (i + 1) % reunit_every == 0) ? 1 : 0;
         if (mode1 && (s = join())) return s;  // stage 1 is about to rewrite the halves
-        launch_stage(prec, 1, mode1, 0, B, cur, alt, accum, clover_base(scratch, Ly), st);
+        launch_stage(prec, 1, mode1, 0, B, cur, alt, accum, clover_base(scratch, Ly), st, grid);
         if ((s = last_launch("stage 1"))) return s;
         if (mode1) {
             TGF_CUDA(cudaEventRecord(sb->fork, st));
@@ -812,9 +823,9 @@ static tgf_status enqueue_flow(int prec, const tgf_lattice* lat, int ncfg, const
             TGF_CUDA(cudaEventRecord(sb->join, sb->s));
             pending = true;
         }
-        launch_stage(prec, 2, 0, 0, B, alt, cur, accum, nullptr, st);
+        launch_stage(prec, 2, 0, 0, B, alt, cur, accum, nullptr, st, grid);
         if ((s = last_launch("stage 2"))) return s;
-        launch_stage(prec, 3, 0, ru, B, cur, alt, accum, nullptr, st);
+        launch_stage(prec, 3, 0, ru, B, cur, alt, accum, nullptr, st, grid);
         if ((s = last_launch("stage 3"))) return s;
         std::swap(cur, alt);
         std::vector<int> fw, fr;

@@ -202,8 +202,9 @@ struct AccStore<float> {
 int set_error(int st, const char* fmt, ...);
 
 // mode: 0 = RK3 stage only; 1 = stage and clover halves of the input field; 2 = halves only
+// grid > 0 launches that many blocks (a grid-stride loop covers B.nblk tiles); 0 = one block per tile
 void launch_stage(int prec, int stage, int mode, int reunit, const Batch& B, const void* w_in, void* w_out,
-                  void* acc, void* clov, cudaStream_t st);
+                  void* acc, void* clov, cudaStream_t st, int grid = 0);
 void launch_clover_sum(int prec, unsigned flags, const Batch& B, const void* clov, double* partial,
                        cudaStream_t st);
 void launch_reduce(const Batch& B, const double* partial, double* obs, cudaStream_t st);

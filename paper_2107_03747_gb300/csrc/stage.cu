@@ -263,50 +263,51 @@ k_stage(const __grid_constant__ BatchT<CAP> B, const typename Store<P>::T* __res
 
 template <int P, int STAGE, int MODE, int CAP>
 static void launch_cap(const Batch& B, const void* w_in, void* w_out, void* acc, void* clov, int reunit,
-                       cudaStream_t st) {
+                       cudaStream_t st, int grid) {
     using T = typename Store<P>::T;
     constexpr int SPB = 32;
+    const int g = (grid > 0 && grid < B.nblk) ? grid : B.nblk;
     if constexpr (CAP == kMaxCfg) {
-        k_stage<P, STAGE, MODE, SPB, kMaxCfg><<<B.nblk, 4 * SPB, 0, st>>>(B, (const T*)w_in, (T*)w_out, (T*)acc,
-                                                                          (T*)clov, reunit);
+        k_stage<P, STAGE, MODE, SPB, kMaxCfg><<<g, 4 * SPB, 0, st>>>(B, (const T*)w_in, (T*)w_out, (T*)acc,
+                                                                     (T*)clov, reunit);
     } else {
         BatchT<CAP> b;
         b.ncfg = B.ncfg;
         b.nblk = B.nblk;
         for (int i = 0; i < B.ncfg; ++i) b.c[i] = B.c[i];
-        k_stage<P, STAGE, MODE, SPB, CAP><<<B.nblk, 4 * SPB, 0, st>>>(b, (const T*)w_in, (T*)w_out, (T*)acc,
-                                                                      (T*)clov, reunit);
+        k_stage<P, STAGE, MODE, SPB, CAP><<<g, 4 * SPB, 0, st>>>(b, (const T*)w_in, (T*)w_out, (T*)acc,
+                                                                 (T*)clov, reunit);
     }
 }
 
 template <int P, int STAGE, int MODE>
 static void launch_m(const Batch& B, const void* w_in, void* w_out, void* acc, void* clov, int reunit,
-                     cudaStream_t st) {
+                     cudaStream_t st, int grid) {
     if (B.ncfg <= kSmallCap)
-        launch_cap<P, STAGE, MODE, kSmallCap>(B, w_in, w_out, acc, clov, reunit, st);
+        launch_cap<P, STAGE, MODE, kSmallCap>(B, w_in, w_out, acc, clov, reunit, st, grid);
     else
-        launch_cap<P, STAGE, MODE, kMaxCfg>(B, w_in, w_out, acc, clov, reunit, st);
+        launch_cap<P, STAGE, MODE, kMaxCfg>(B, w_in, w_out, acc, clov, reunit, st, grid);
 }
 
 template <int P>
 static void launch_stage_p(int stage, int mode, int reunit, const Batch& B, const void* w_in, void* w_out,
-                           void* acc, void* clov, cudaStream_t st) {
-    if (mode == 2) return launch_m<P, 1, 2>(B, w_in, w_out, acc, clov, reunit, st);
+                           void* acc, void* clov, cudaStream_t st, int grid) {
+    if (mode == 2) return launch_m<P, 1, 2>(B, w_in, w_out, acc, clov, reunit, st, grid);
     switch (stage) {
         case 1:
-            if (mode == 1) launch_m<P, 1, 1>(B, w_in, w_out, acc, clov, reunit, st);
-            else launch_m<P, 1, 0>(B, w_in, w_out, acc, clov, reunit, st);
+            if (mode == 1) launch_m<P, 1, 1>(B, w_in, w_out, acc, clov, reunit, st, grid);
+            else launch_m<P, 1, 0>(B, w_in, w_out, acc, clov, reunit, st, grid);
             break;
-        case 2: launch_m<P, 2, 0>(B, w_in, w_out, acc, clov, reunit, st); break;
-        default: launch_m<P, 3, 0>(B, w_in, w_out, acc, clov, reunit, st); break;
+        case 2: launch_m<P, 2, 0>(B, w_in, w_out, acc, clov, reunit, st, grid); break;
+        default: launch_m<P, 3, 0>(B, w_in, w_out, acc, clov, reunit, st, grid); break;
     }
 }
 
 void launch_stage(int prec, int stage, int mode, int reunit, const Batch& B, const void* w_in, void* w_out,
-                  void* acc, void* clov, cudaStream_t st) {
-    if (prec == P64) launch_stage_p<P64>(stage, mode, reunit, B, w_in, w_out, acc, clov, st);
-    else if (prec == P32) launch_stage_p<P32>(stage, mode, reunit, B, w_in, w_out, acc, clov, st);
-    else launch_stage_p<P32R12>(stage, mode, reunit, B, w_in, w_out, acc, clov, st);
+                  void* acc, void* clov, cudaStream_t st, int grid) {
+    if (prec == P64) launch_stage_p<P64>(stage, mode, reunit, B, w_in, w_out, acc, clov, st, grid);
+    else if (prec == P32) launch_stage_p<P32>(stage, mode, reunit, B, w_in, w_out, acc, clov, st, grid);
+    else launch_stage_p<P32R12>(stage, mode, reunit, B, w_in, w_out, acc, clov, st, grid);
 }
 
 }  // namespace tgf

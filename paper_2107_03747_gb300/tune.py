@@ -1,0 +1,105 @@
+"""Launch tuner of tgf_flow: times the launch settings on the actual workload and caches the winner.
+
+The settings (tgf.h: TGF_TUNE_GRID(k), TGF_TUNE_SIZE_ORDER) change how the stage kernels are
+scheduled, never what they compute: a persistent grid of k x SMs x resident blocks that loops
+over the 32-site tiles (k = 0: one block per tile), and the order of the configurations inside
+each launch (as given, or largest first).  For a workload -- precision, the multiset of
+extents, measurement interval -- the tuner flows the batch for a few steps under every
+candidate (each captured as its own CUDA graph), times the best of `reps` replays with CUDA
+events, and stores the fastest flags in a JSON cache (path from TGF_TUNE_CACHE, else
+~/.cache/tgf/tune.json).  Later calls with the same workload read the cache.
+"""
+from __future__ import annotations
+
+import json
+import os
+from collections import Counter
+
+GRIDS = (0, 1, 2, 4)
+ORDERS = (False, True)
+TGF_TUNE_SIZE_ORDER = 1 << 12
+
+
+def tune_flags(grid: int, by_size: bool) -> int:
+    return ((grid & 0xF) << 8) | (TGF_TUNE_SIZE_ORDER if by_size else 0)
+
+
+def candidates():
+    return [tune_flags(g, o) for g in GRIDS for o in ORDERS]
+
+
+def workload_key(prec: int, Ls, measure_every: int) -> str:
+    ext = sorted(Counter(tuple(int(x) for x in L) for L in Ls).items())
+    return json.dumps({"prec": int(prec), "extents": [[list(e), n] for e, n in ext], "measure_every": int(measure_every)},
+                      sort_keys=True)
+
+
+def cache_path() -> str:
+    return os.environ.get("TGF_TUNE_CACHE", os.path.join(os.path.expanduser("~"), ".cache", "tgf", "tune.json"))
+
+
+def load_cache(path: str | None = None) -> dict:
+    path = path or cache_path()
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return d if isinstance(d, dict) else {}
+    except (OSError, ValueError):
+        return {}
+
+
+def store(key: str, entry: dict, path: str | None = None) -> None:
+    path = path or cache_path()
+    d = load_cache(path)
+    d[key] = entry
+    os.makedirs(os.path.dirname(os.path.abspath(path)), exist_ok=True)
+    tmp = path + ".tmp"
+    with open(tmp, "w") as f:
+        json.dump(d, f, indent=1, sort_keys=True)
+    os.replace(tmp, path)
+
+
+def choose(times: dict) -> int:
+    """The fastest candidate; ties go to the simplest (smaller flag value)."""
+    return min(sorted(times), key=lambda f: times[f])
+
+
+def tune(batch, eps: float = 0.01, steps: int = 4, measure_every: int = 1, reps: int = 3, path: str | None = None,
+         timer=None, force: bool = False) -> int:
+    """Best tgf_flow flags for `batch` (a binding.FlowBatch); the batch's fields are restored afterwards.
+
+    `timer(flags) -> ms` replaces the GPU timing (tests on the host)."""
+    key = workload_key(batch.prec, batch.Ls, measure_every)
+    if not force:
+        hit = load_cache(path).get(key)
+        if hit is not None:
+            return int(hit["flags"])
+    if timer is None:
+        timer = _gpu_timer(batch, eps, steps, measure_every, reps)
+    times = {f: float(timer(f)) for f in candidates()}
+    best = choose(times)
+    store(key, {"flags": best, "ms": {str(f): t for f, t in times.items()}, "steps": steps}, path)
+    return best
+
+
+def _gpu_timer(batch, eps, steps, measure_every, reps):
+    import torch
+
+    saved = batch.links.clone()
+    t_end = eps * steps
+
+    def run(flags):
+        best = float("inf")
+        for r in range(reps + 1):
+            batch.links.copy_(saved)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            batch.flow(eps, t_end, measure_every=measure_every, flags=flags)
+            b.record()
+            torch.cuda.synchronize()
+            if r:  # the first run captures the graph
+                best = min(best, a.elapsed_time(b))
+        batch.links.copy_(saved)
+        return best
+
+    return run

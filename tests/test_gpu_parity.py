@@ -438,3 +438,28 @@ def test_checkpoint_resume_is_bitwise_identical(tgf, prec, tmp_path):
     assert np.array_equal(c.get_links()[0], b.get_links()[0])
     c.flow(0.01, 0.06)
     assert np.array_equal(a.get_links()[0], c.get_links()[0])
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_launch_tuning_settings_give_identical_flows(tgf, prec, tmp_path):
+    """Every launch setting of the tuner (persistent grids, configurations by size) computes the
+    same flow bit for bit; the tuner returns one of them and caches it."""
+    from paper_2107_03747_gb300 import tune
+
+    Ls = [(4, 4, 12, 12), (6, 6, 18, 18), (2, 2, 6, 6), (4, 4, 12, 12)]
+    fields = [I.random_links(L, 70 + i, 0.5) for i, L in enumerate(Ls)]
+    t_end = [0.05, 0.03, 0.04, 0.05]
+    ref = None
+    for f in tune.candidates():
+        b = load(tgf, Ls, fields, prec)
+        obs, nrec = b.flow(0.01, t_end, flags=f)
+        got = (b.get_links(), obs.cpu().numpy(), list(nrec))
+        if ref is None:
+            ref = got
+            continue
+        assert all(np.array_equal(x, y) for x, y in zip(ref[0], got[0]))
+        assert np.array_equal(ref[1], got[1]) and ref[2] == got[2]
+    b = load(tgf, Ls, fields, prec)
+    best = tune.tune(b, eps=0.01, steps=3, path=str(tmp_path / "tune.json"))
+    assert best in tune.candidates()
+    assert all(np.array_equal(x, y) for x, y in zip(b.get_links(), fields)) or prec == "fp32"
