@@ -13,6 +13,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/tgf.h"
 #include "lattice.cuh"
 
@@ -21,6 +23,14 @@ using namespace tgf;
 namespace {
 
 thread_local std::string g_err;
+
+// NVTX range over one ABI call (visible in Nsight Systems / Compute timelines; no cost without a tool)
+struct Range {
+    explicit Range(const char* name) { nvtxRangePushA(name); }
+    ~Range() { nvtxRangePop(); }
+    Range(const Range&) = delete;
+    Range& operator=(const Range&) = delete;
+};
 
 tgf_status fail(tgf_status st, const char* fmt, ...) {
     char buf[512];
@@ -300,6 +310,7 @@ tgf_status tgf_canonical_bytes(const tgf_lattice* lat, size_t* bytes) {
 }
 
 tgf_status tgf_pack(int prec, const tgf_lattice* lat, int ncfg, const double* canon_dev, void* links, void* stream) {
+    Range range_("tgf_pack");
     tgf_status s;
     if ((s = check_prec(prec)) || (s = check_lat(lat, ncfg)) || (s = check_ptr(canon_dev, "canon_dev")) ||
         (s = check_ptr(links, "links")))
@@ -312,6 +323,7 @@ tgf_status tgf_pack(int prec, const tgf_lattice* lat, int ncfg, const double* ca
 }
 
 tgf_status tgf_unpack(int prec, const tgf_lattice* lat, int ncfg, const void* links, double* canon_dev, void* stream) {
+    Range range_("tgf_unpack");
     tgf_status s;
     if ((s = check_prec(prec)) || (s = check_lat(lat, ncfg)) || (s = check_ptr(canon_dev, "canon_dev")) ||
         (s = check_ptr(links, "links")))
@@ -334,6 +346,7 @@ static tgf_status check_staging(const tgf_lattice* lat, int ncfg, const double* 
 
 tgf_status tgf_upload(int prec, const tgf_lattice* lat, int ncfg, const double* canon_host, double* staging_dev,
                       size_t staging_bytes, void* links, void* stream) {
+    Range range_("tgf_upload");
     tgf_status s;
     if ((s = check_prec(prec)) || (s = check_lat(lat, ncfg)) || (s = check_ptr(links, "links")) ||
         (s = check_staging(lat, ncfg, staging_dev, staging_bytes)))
@@ -354,6 +367,7 @@ tgf_status tgf_upload(int prec, const tgf_lattice* lat, int ncfg, const double* 
 
 tgf_status tgf_download(int prec, const tgf_lattice* lat, int ncfg, const void* links, double* staging_dev,
                         size_t staging_bytes, double* canon_host, void* stream) {
+    Range range_("tgf_download");
     tgf_status s;
     if ((s = check_prec(prec)) || (s = check_lat(lat, ncfg)) || (s = check_ptr(links, "links")) ||
         (s = check_staging(lat, ncfg, staging_dev, staging_bytes)))
@@ -375,6 +389,7 @@ tgf_status tgf_download(int prec, const tgf_lattice* lat, int ncfg, const void* 
 
 tgf_status tgf_stage(int prec, const tgf_lattice* lat, int ncfg, const void* w_in, void* w_out, void* accum, int stage,
                      double eps, int reunit, void* stream) {
+    Range range_("tgf_stage");
     tgf_status s;
     if ((s = check_prec(prec)) || (s = check_lat(lat, ncfg)) || (s = check_ptr(w_in, "w_in")) ||
         (s = check_ptr(w_out, "w_out")) || (s = check_ptr(accum, "accum")))
@@ -392,6 +407,7 @@ tgf_status tgf_stage(int prec, const tgf_lattice* lat, int ncfg, const void* w_i
 tgf_status tgf_measure(int prec, const tgf_lattice* lat, int ncfg, const void* links, double* scratch,
                        size_t scratch_bytes, tgf_obs* obs_dev, size_t obs_stride, int rec, double t, unsigned flags,
                        void* stream) {
+    Range range_("tgf_measure");
     tgf_status s;
     if ((s = check_prec(prec)) || (s = check_lat(lat, ncfg)) || (s = check_ptr(links, "links")) ||
         (s = check_ptr(scratch, "scratch")) || (s = check_ptr(obs_dev, "obs_dev")))
@@ -453,6 +469,7 @@ uint32_t tgf_crc32(const void* data, size_t n) {
 
 tgf_status tgf_save(const char* path, int prec, const tgf_lattice* lat, int ncfg, const void* links, double* staging_dev,
                     size_t staging_bytes, double t, long long step, unsigned long long seed, void* stream) {
+    Range range_("tgf_save");
     tgf_status s;
     if (!path) return fail(TGF_EINVAL, "path is NULL");
     if ((s = check_prec(prec)) || (s = check_lat(lat, ncfg)) || (s = check_ptr(links, "links"))) return s;
@@ -491,6 +508,7 @@ tgf_status tgf_save(const char* path, int prec, const tgf_lattice* lat, int ncfg
 
 tgf_status tgf_load(const char* path, int prec, const tgf_lattice* lat, int ncfg, void* links, double* staging_dev,
                     size_t staging_bytes, double* t, long long* step, unsigned long long* seed, void* stream) {
+    Range range_("tgf_load");
     tgf_status s;
     if (!path) return fail(TGF_EINVAL, "path is NULL");
     if ((s = check_prec(prec)) || (s = check_lat(lat, ncfg)) || (s = check_ptr(links, "links"))) return s;
@@ -643,6 +661,7 @@ tgf_status tgf_sun_unpack(int N, const tgf_lattice* lat, int ncfg, const void* l
 
 tgf_status tgf_sun_stage(int N, const tgf_lattice* lat, int ncfg, const void* w_in, void* w_out, void* accum, int stage,
                          double eps, void* stream) {
+    Range range_("tgf_sun_stage");
     tgf_status s;
     if ((s = check_n(N)) || (s = check_lat(lat, ncfg)) || (s = check_ptr(w_in, "w_in")) ||
         (s = check_ptr(w_out, "w_out")) || (s = check_ptr(accum, "accum")))
@@ -660,6 +679,7 @@ tgf_status tgf_sun_stage(int N, const tgf_lattice* lat, int ncfg, const void* w_
 tgf_status tgf_sun_measure(int N, const tgf_lattice* lat, int ncfg, const void* links, double* scratch,
                            size_t scratch_bytes, tgf_obs* obs_dev, size_t obs_stride, int rec, double t, unsigned flags,
                            void* stream) {
+    Range range_("tgf_sun_measure");
     tgf_status s;
     if ((s = check_n(N)) || (s = check_lat(lat, ncfg)) || (s = check_ptr(links, "links")) ||
         (s = check_ptr(scratch, "scratch")) || (s = check_ptr(obs_dev, "obs_dev")))
@@ -680,6 +700,7 @@ tgf_status tgf_sun_measure(int N, const tgf_lattice* lat, int ncfg, const void* 
 
 tgf_status tgf_mc_sweeps(int prec, const tgf_lattice* lat, int ncfg, void* links, double beta, int n_hybrid, int n_or,
                          unsigned long long seed, unsigned long long first_sweep, void* stream) {
+    Range range_("tgf_mc_sweeps");
     tgf_status s;
     if ((s = check_lat(lat, ncfg)) || (s = check_ptr(links, "links"))) return s;
     if (prec != TGF_FP64) return fail(TGF_EINVAL, "the Monte Carlo update needs TGF_FP64 storage (got precision %d)", prec);
@@ -710,6 +731,7 @@ tgf_status tgf_mc_sweeps(int prec, const tgf_lattice* lat, int ncfg, void* links
 tgf_status tgf_measure_slices(int prec, const tgf_lattice* lat, int ncfg, const void* links, double* scratch,
                               size_t scratch_bytes, int dir, double* q_dev, size_t q_stride, unsigned flags,
                               void* stream) {
+    Range range_("tgf_measure_slices");
     tgf_status s;
     if ((s = check_prec(prec)) || (s = check_lat(lat, ncfg)) || (s = check_ptr(links, "links")) ||
         (s = check_ptr(scratch, "scratch")) || (s = check_ptr(q_dev, "q_dev")))
@@ -853,6 +875,7 @@ static tgf_status enqueue_flow(int prec, const tgf_lattice* lat, int ncfg, const
 tgf_status tgf_flow(int prec, const tgf_lattice* lat, int ncfg, void* w, void* w_tmp, void* accum, double* scratch,
                     size_t scratch_bytes, double eps, const double* t_end, int measure_every, int reunit_every,
                     unsigned flags, tgf_obs* obs_dev, size_t obs_cap, int* n_records, void* stream) {
+    Range range_("tgf_flow");
     tgf_status s;
     if ((s = check_prec(prec)) || (s = check_lat(lat, ncfg)) || (s = check_ptr(w, "w")) ||
         (s = check_ptr(w_tmp, "w_tmp")) || (s = check_ptr(accum, "accum")) || (s = check_ptr(scratch, "scratch")) ||
