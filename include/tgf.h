@@ -196,7 +196,8 @@ tgf_status tgf_flow_records(double eps, double t_end, int measure_every, int *n_
 /* The paper defines the coupling for SU(N) on the l x l x (Nl) x (Nl) box with the twist
  * exp(2 pi i k / N) and gives numbers for N = 3; these calls run the same flow and measurement
  * for N = 2, 3, 4 in FP64: Z = -P_ta(U Sigma) with the 1/N trace, Luscher's RK3 as in tgf_stage,
- * exp(X) by its Taylor series after scaling X by 2^-s to ||X||_F <= 1/2 and squaring back, the
+ * exp(X) by its Taylor series after scaling X by 2^-s to ||X||_F <= 1/2 and squaring back
+ * (N = 2: the closed form e^{i tau}(cos theta + sin theta / theta X0)), the
  * twisted clover and plaquette as in tgf_measure with the twist n_{mu nu} taken mod N and
  * P = (1/(6V)) sum_n sum_{mu<nu} (1/N) Re Tr[Z* P_{mu nu}].  Canonical buffers hold V x 4 x N x N
  * complex doubles per configuration ([x3][x2][x1][x0][mu][row][col][re,im]); device storage is

@@ -6,7 +6,7 @@
 // definitions as the SU(3) kernels (twisted staples, Z = -P_ta(U Sigma) with the 1/N trace,
 // Luscher's low-storage RK3, W' = exp(X) W, the clover G = -(i/8)(C - C^+), E, q and the twisted
 // plaquette), written for N x N matrices in registers.  The exponential is summed as its Taylor
-// series after scaling by 2^-s to ||X||_F <= 1/2, then squared s times.
+// series after scaling by 2^-s to ||X||_F <= 1/2, then squared s times (SU(2): closed form).
 //
 // Storage per configuration and direction: N^2 double2 planes (matrix entries, row-major) of
 // Vp sites; the RK3 accumulator X holds N^2 reals per link: the imaginary parts of the N
@@ -177,6 +177,27 @@ __device__ void expN(matN<N>& out, const matN<N>& X) {
         t2 = out;
         nnN<N, false>(out, t2, t2);
     }
+}
+
+// SU(2): closed form.  X = i tau 1 + X0 with X0 traceless anti-Hermitian, X0^2 = -theta^2 1
+// (theta^2 = a^2 + |b|^2 for X0 = [[i a, b], [-b*, -i a]]), so
+// exp(X) = e^{i tau} (cos theta 1 + (sin theta / theta) X0).
+template <>
+__device__ void expN<2>(matN<2>& out, const matN<2>& X) {
+    const double tau = 0.5 * (X.e[0][0].im + X.e[1][1].im);
+    const double a = X.e[0][0].im - tau;
+    const double br = X.e[0][1].re, bi = X.e[0][1].im;
+    const double th = sqrt(a * a + br * br + bi * bi);
+    const double c = cos(th), sn = th > 1e-30 ? sin(th) / th : 1.0;
+    double er, ei;
+    sincos(tau, &ei, &er);
+    // M = c 1 + sn X0;  out = e^{i tau} M
+    const cx<double> m00 = {c, sn * a}, m11 = {c, -sn * a};
+    const cx<double> m01 = {sn * br, sn * bi}, m10 = {-sn * br, sn * bi};
+    out.e[0][0] = {er * m00.re - ei * m00.im, er * m00.im + ei * m00.re};
+    out.e[0][1] = {er * m01.re - ei * m01.im, er * m01.im + ei * m01.re};
+    out.e[1][0] = {er * m10.re - ei * m10.im, er * m10.im + ei * m10.re};
+    out.e[1][1] = {er * m11.re - ei * m11.im, er * m11.im + ei * m11.re};
 }
 
 // one RK3 stage for SU(N); block = 4 warps (one per direction) x 32 sites

@@ -463,3 +463,19 @@ def test_launch_tuning_settings_give_identical_flows(tgf, prec, tmp_path):
     best = tune.tune(b, eps=0.01, steps=3, path=str(tmp_path / "tune.json"))
     assert best in tune.candidates()
     assert all(np.array_equal(x, y) for x, y in zip(b.get_links(), fields)) or prec == "fp32"
+
+
+def test_large_batch_uses_the_full_descriptor_and_matches_oracle(tgf):
+    """More than 16 configurations take the 256-entry launch descriptor; 40 small mixed
+    configurations, one RK3 step and a measurement each, against the oracle."""
+    Ls = [(2, 2, 6, 6) if i % 3 else (4, 4, 12, 12) for i in range(40)]
+    fields = [I.random_links(L, 300 + i, 0.6) for i, L in enumerate(Ls)]
+    b = load(tgf, Ls, fields, "fp64")
+    for st in (1, 2, 3):
+        b.stage(st, 0.02)
+    got = b.get_links()
+    m = b.measure(0.02)
+    for i in range(len(Ls)):
+        ref = O.rk3_step(fields[i], 0.02, TW)
+        assert np.abs(got[i] - ref).max() <= 1e-12
+        close_obs(m[i], O.measure(ref, TW))
