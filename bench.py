@@ -464,11 +464,11 @@ def run_tgf(args):
     if rank == 0:
         cpu = None
         if not args.no_cpu:
-            s, t = oracle_sample(members, 1)
+            s, t = oracle_sample(members, 3)
             L0 = members[0][0]
             cpu = {"value": s / t, "unit": "site-steps/s", "cores": 1, "kind": "oracle",
-                   "sample": f"one RK3 step + one measurement of one {L0[0]}x{L0[1]}x{L0[2]}x{L0[3]} configuration "
-                             f"({s} site-steps, {t:.1f} s, numpy FP64 single-threaded)"}
+                   "sample": f"three RK3 steps, each with a measurement, of one {L0[0]}x{L0[1]}x{L0[2]}x{L0[3]} "
+                             f"configuration ({s} site-steps, {t:.1f} s, numpy FP64 single-threaded)"}
         canon_bytes = canon_host.numel() * 8
         link_bytes = tgf.tgf_links_bytes(prec, b.lat)
         line = {
