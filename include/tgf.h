@@ -241,6 +241,17 @@ tgf_status tgf_sun_measure(int N, const tgf_lattice *lat, int ncfg, const void *
 tgf_status tgf_mc_sweeps(int prec, const tgf_lattice *lat, int ncfg, void *links, double beta, int n_hybrid,
                          int n_or, unsigned long long seed, unsigned long long first_sweep, void *stream);
 
+/* ---- self-checking builds ---------------------------------------------------------------- */
+
+/* A library compiled with -DTGF_CHECK checks the site index of every link, accumulator and
+ * clover access against the plane length in the kernels; a violation is recorded in a device
+ * word of the kernel's source file and the access is redirected to site 0 (no fault).  This call
+ * synchronises the device and returns the words as bits (1 stage kernels, 2 measurement, 4
+ * layout, 8 Monte Carlo, 16 SU(N)) and clears them; 0 means no violation since the last call.
+ * In a normal build it returns TGF_EINVAL.  The paper has no counterpart: it replaces a memory
+ * checker where none can run. */
+tgf_status tgf_check_errors(unsigned int *bits);
+
 /* ---- checkpoints --------------------------------------------------------------------------- */
 
 /* Between RK3 steps the state of a flow is the field alone (X is rebuilt by stage 1), so a

@@ -74,6 +74,7 @@ _SIGS = {
     "tgf_save": [C.c_char_p, C.c_int, _LATP, C.c_int, _P, _P, _SZ, C.c_double, C.c_longlong, C.c_ulonglong, _P],
     "tgf_load": [C.c_char_p, C.c_int, _LATP, C.c_int, _P, _P, _SZ, C.POINTER(C.c_double), C.POINTER(C.c_longlong),
                  C.POINTER(C.c_ulonglong), _P],
+    "tgf_check_errors": [C.POINTER(C.c_uint)],
     "tgf_norm": [C.c_double, C.c_int, C.c_int, C.POINTER(C.c_double)],
     "tgf_fma_peak": [C.c_int, _P, C.c_int, C.c_int, C.POINTER(C.c_double), _P],
     "tgf_lambda": [C.c_double, C.c_int, C.c_double, C.POINTER(C.c_double), C.POINTER(C.c_double), C.c_int,
@@ -319,6 +320,13 @@ class SunBatch:
         _check(_lib.tgf_sun_measure(self.N, self.lat, n, _ptr(self.links), _ptr(self.scratch),
                                     self.scratch.numel(), _ptr(obs), 1, 0, t, flags, _stream(stream)))
         return obs.cpu().numpy().reshape(n, 5)
+
+
+def tgf_check_errors() -> int:
+    """Bits of the kernel files that recorded an out-of-range site index (self-checking builds)."""
+    b = C.c_uint()
+    _check(_lib.tgf_check_errors(C.byref(b)))
+    return b.value
 
 
 def tgf_crc32(data: bytes) -> int:

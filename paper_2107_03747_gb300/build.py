@@ -27,10 +27,14 @@ def nvcc() -> str:
     raise RuntimeError("nvcc not found")
 
 
-def _compile(src: str, verbose_ptxas: bool) -> str:
-    obj = os.path.join(BUILD, os.path.splitext(src)[0] + ".o")
+LIB_CHECK = os.path.join(PKG, "libtgf_check.so")
+BUILD_CHECK = os.path.join(PKG, "_build_check")
+
+
+def _compile(src: str, verbose_ptxas: bool, check: bool = False) -> str:
+    obj = os.path.join(BUILD_CHECK if check else BUILD, os.path.splitext(src)[0] + ".o")
     cmd = [nvcc(), "-c", os.path.join(CSRC, src), "-o", obj, "-O3", "-std=c++17", "-Xcompiler", "-fPIC",
-           "-I", os.path.join(ROOT, "include")]
+           "-I", os.path.join(ROOT, "include")] + (["-DTGF_CHECK"] if check else [])
     if src.endswith(".cu"):
         cmd += ARCH + ["-lineinfo"]
         if verbose_ptxas:
@@ -45,23 +49,25 @@ def _compile(src: str, verbose_ptxas: bool) -> str:
     return obj
 
 
-def build(verbose_ptxas: bool = False, force: bool = False) -> str:
-    """Compile every source and link libtgf.so; returns the library path."""
-    os.makedirs(BUILD, exist_ok=True)
+def build(verbose_ptxas: bool = False, force: bool = False, check: bool = False) -> str:
+    """Compile every source and link libtgf.so (check=True: the self-checking libtgf_check.so,
+    compiled with -DTGF_CHECK); returns the library path."""
+    lib = LIB_CHECK if check else LIB
+    os.makedirs(BUILD_CHECK if check else BUILD, exist_ok=True)
     deps = [os.path.join(CSRC, f) for f in os.listdir(CSRC)] + [os.path.join(ROOT, "include", "tgf.h")]
-    if not force and os.path.exists(LIB):
-        lib_t = os.path.getmtime(LIB)
+    if not force and os.path.exists(lib):
+        lib_t = os.path.getmtime(lib)
         if all(os.path.getmtime(d) <= lib_t for d in deps):
-            return LIB
+            return lib
     with ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
-        objs = list(ex.map(lambda s: _compile(s, verbose_ptxas), SOURCES))
-    tmp = LIB + ".tmp"
+        objs = list(ex.map(lambda s: _compile(s, verbose_ptxas, check), SOURCES))
+    tmp = lib + ".tmp"
     cmd = [nvcc(), "-shared", "-o", tmp] + objs + ARCH + ["-Xcompiler", "-fPIC"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

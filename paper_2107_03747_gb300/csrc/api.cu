@@ -423,6 +423,25 @@ tgf_status tgf_measure(int prec, const tgf_lattice* lat, int ncfg, const void* l
                            (cudaStream_t)stream);
 }
 
+// ---- self-checking builds ------------------------------------------------------------------
+
+tgf_status tgf_check_errors(unsigned* bits) {
+    if (!bits) return fail(TGF_EINVAL, "bits is NULL");
+#ifdef TGF_CHECK
+    TGF_CUDA(cudaDeviceSynchronize());
+    const unsigned w[5] = {check_word_stage(), check_word_measure(), check_word_pack(), check_word_mc(),
+                           check_word_sun()};
+    unsigned b = 0;
+    for (int i = 0; i < 5; ++i)
+        if (w[i]) b |= 1u << i;
+    *bits = b;
+    return TGF_OK;
+#else
+    *bits = 0;
+    return fail(TGF_EINVAL, "not a self-checking build (compile the library with -DTGF_CHECK)");
+#endif
+}
+
 // ---- checkpoints ---------------------------------------------------------------------------
 
 namespace {

@@ -76,6 +76,41 @@ __device__ __forceinline__ void centre(int k, T& zr, T& zi) {
 }
 
 // ---------------------------------------------------------------------------------------------
+// self-checking builds (-DTGF_CHECK): every link, accumulator and clover access checks its site
+// index against the plane length.  A violation sets bit 0 of the translation unit's check word
+// and the access goes to site 0 instead, so nothing faults; tgf_check_errors() reads and clears
+// the words.  Without TGF_CHECK the checks compile to nothing.
+// ---------------------------------------------------------------------------------------------
+
+#ifdef TGF_CHECK
+static __device__ unsigned int g_tgf_check;
+__device__ __forceinline__ int checked_site(int s, int n) {
+    if ((unsigned)s < (unsigned)n) return s;
+    atomicOr(&g_tgf_check, 1u);
+    return 0;
+}
+// host: this translation unit's check word, cleared after reading (~0u if the copy fails)
+static inline unsigned check_word_read_and_clear() {
+    unsigned v = 0, z = 0;
+    if (cudaMemcpyFromSymbol(&v, g_tgf_check, sizeof v) != cudaSuccess) return ~0u;
+    if (cudaMemcpyToSymbol(g_tgf_check, &z, sizeof z) != cudaSuccess) return ~0u;
+    return v;
+}
+#define TGF_CHECK_WORD(name) \
+    unsigned check_word_##name() { return check_word_read_and_clear(); }
+#else
+__device__ __forceinline__ int checked_site(int s, int) { return s; }
+#define TGF_CHECK_WORD(name)
+#endif
+
+// per translation unit check words of a self-checking build
+unsigned check_word_stage();
+unsigned check_word_measure();
+unsigned check_word_pack();
+unsigned check_word_mc();
+unsigned check_word_sun();
+
+// ---------------------------------------------------------------------------------------------
 // storage traits: load / store a link of direction mu at site s
 // ---------------------------------------------------------------------------------------------
 
@@ -87,6 +122,7 @@ struct Store<P64> {
     using T = double;
     static constexpr int reals = 18;
     static __device__ __forceinline__ void load(const double* __restrict__ base, int Vp, int s, mat3<double>& u) {
+        s = checked_site(s, Vp);
         const double2* q = reinterpret_cast<const double2*>(base);
 #pragma unroll
         for (int k = 0; k < 9; ++k) {
@@ -95,6 +131,7 @@ struct Store<P64> {
         }
     }
     static __device__ __forceinline__ void store(double* __restrict__ base, int Vp, int s, const mat3<double>& u) {
+        s = checked_site(s, Vp);
         double2* q = reinterpret_cast<double2*>(base);
 #pragma unroll
         for (int k = 0; k < 9; ++k) q[(size_t)k * Vp + s] = make_double2(u.e[k / 3][k % 3].re, u.e[k / 3][k % 3].im);
@@ -106,6 +143,7 @@ struct Store<P32> {
     using T = float;
     static constexpr int reals = 18;
     static __device__ __forceinline__ void load(const float* __restrict__ base, int Vp, int s, mat3<float>& u) {
+        s = checked_site(s, Vp);
         const float4* q = reinterpret_cast<const float4*>(base);
 #pragma unroll
         for (int g = 0; g < 4; ++g) {
@@ -117,6 +155,7 @@ struct Store<P32> {
         u.e[2][2] = {w.x, w.y};
     }
     static __device__ __forceinline__ void store(float* __restrict__ base, int Vp, int s, const mat3<float>& u) {
+        s = checked_site(s, Vp);
         float4* q = reinterpret_cast<float4*>(base);
 #pragma unroll
         for (int g = 0; g < 4; ++g)
@@ -132,6 +171,7 @@ struct Store<P32R12> {
     using T = float;
     static constexpr int reals = 12;
     static __device__ __forceinline__ void load(const float* __restrict__ base, int Vp, int s, mat3<float>& u) {
+        s = checked_site(s, Vp);
         const float4* q = reinterpret_cast<const float4*>(base);
 #pragma unroll
         for (int g = 0; g < 3; ++g) {
@@ -142,6 +182,7 @@ struct Store<P32R12> {
         rebuild_row2(u);
     }
     static __device__ __forceinline__ void store(float* __restrict__ base, int Vp, int s, const mat3<float>& u) {
+        s = checked_site(s, Vp);
         float4* q = reinterpret_cast<float4*>(base);
 #pragma unroll
         for (int g = 0; g < 3; ++g)
@@ -158,6 +199,7 @@ struct AccStore;
 template <>
 struct AccStore<double> {
     static __device__ __forceinline__ void load(const double* __restrict__ base, int Vp, int s, alg8<double>& x) {
+        s = checked_site(s, Vp);
         const double2* q = reinterpret_cast<const double2*>(base);
 #pragma unroll
         for (int g = 0; g < 4; ++g) {
@@ -167,6 +209,7 @@ struct AccStore<double> {
         }
     }
     static __device__ __forceinline__ void store(double* __restrict__ base, int Vp, int s, const alg8<double>& x) {
+        s = checked_site(s, Vp);
         double2* q = reinterpret_cast<double2*>(base);
 #pragma unroll
         for (int g = 0; g < 4; ++g) q[(size_t)g * Vp + s] = make_double2(x.v[2 * g], x.v[2 * g + 1]);
@@ -176,6 +219,7 @@ struct AccStore<double> {
 template <>
 struct AccStore<float> {
     static __device__ __forceinline__ void load(const float* __restrict__ base, int Vp, int s, alg8<float>& x) {
+        s = checked_site(s, Vp);
         const float4* q = reinterpret_cast<const float4*>(base);
 #pragma unroll
         for (int g = 0; g < 2; ++g) {
@@ -187,6 +231,7 @@ struct AccStore<float> {
         }
     }
     static __device__ __forceinline__ void store(float* __restrict__ base, int Vp, int s, const alg8<float>& x) {
+        s = checked_site(s, Vp);
         float4* q = reinterpret_cast<float4*>(base);
 #pragma unroll
         for (int g = 0; g < 2; ++g)

@@ -225,4 +225,6 @@ void launch_mc(int overrelax, const Batch& B, double* w, int mu, int parity, dou
     }
 }
 
+TGF_CHECK_WORD(mc)
+
 }  // namespace tgf

@@ -250,4 +250,6 @@ void launch_reduce(const Batch& B, const double* partial, double* obs, cudaStrea
     }
 }
 
+TGF_CHECK_WORD(measure)
+
 }  // namespace tgf

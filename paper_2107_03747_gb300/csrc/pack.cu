@@ -88,4 +88,6 @@ void launch_unpack(int prec, const Batch& B, const void* w, double* canon, cudaS
     else unpack_p<P32R12>(B, w, canon, st);
 }
 
+TGF_CHECK_WORD(pack)
+
 }  // namespace tgf

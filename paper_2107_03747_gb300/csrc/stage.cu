@@ -72,6 +72,7 @@ __constant__ int8_t c_clover_owner[4][4] = {{0, 1, 1, 0}, {0, 0, 1, 1}, {0, 0, 0
 // written to 9 component planes of length Vp.
 template <class T>
 __device__ __forceinline__ void store_ah(T* __restrict__ p, int Vp, int s, const mat3<T>& d) {
+    s = checked_site(s, Vp);
     p[0 * (size_t)Vp + s] = T(2) * d.e[0][0].im;
     p[1 * (size_t)Vp + s] = T(2) * d.e[1][1].im;
     p[2 * (size_t)Vp + s] = T(2) * d.e[2][2].im;
@@ -309,5 +310,7 @@ void launch_stage(int prec, int stage, int mode, int reunit, const Batch& B, con
     else if (prec == P32) launch_stage_p<P32>(stage, mode, reunit, B, w_in, w_out, acc, clov, st, grid);
     else launch_stage_p<P32R12>(stage, mode, reunit, B, w_in, w_out, acc, clov, st, grid);
 }
+
+TGF_CHECK_WORD(stage)
 
 }  // namespace tgf

@@ -113,6 +113,7 @@ __device__ __forceinline__ void addN(matN<N>& a, const matN<N>& b) {
 
 template <int N>
 __device__ __forceinline__ void loadN(const double* __restrict__ base, int Vp, int dir, int s, matN<N>& u) {
+    s = checked_site(s, Vp);
     const double2* q = reinterpret_cast<const double2*>(base) + (size_t)dir * N * N * Vp;
 #pragma unroll
     for (int k = 0; k < N * N; ++k) {
@@ -122,6 +123,7 @@ __device__ __forceinline__ void loadN(const double* __restrict__ base, int Vp, i
 }
 template <int N>
 __device__ __forceinline__ void storeN(double* __restrict__ base, int Vp, int dir, int s, const matN<N>& u) {
+    s = checked_site(s, Vp);
     double2* q = reinterpret_cast<double2*>(base) + (size_t)dir * N * N * Vp;
 #pragma unroll
     for (int k = 0; k < N * N; ++k) q[(size_t)k * Vp + s] = make_double2(u.e[k / N][k % N].re, u.e[k / N][k % N].im);
@@ -562,5 +564,7 @@ void launch_sun_measure(int N, const Batch& Bm, const Batch& Br, const double* w
 void launch_sun_layout(int N, bool to_storage, const Batch& B, double* canon, double* w, cudaStream_t st) {
     sun_any(N, 2, 0, to_storage, B, B, nullptr, w, canon, nullptr, 0, st);
 }
+
+TGF_CHECK_WORD(sun)
 
 }  // namespace tgf

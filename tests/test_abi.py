@@ -211,3 +211,10 @@ def test_load_rejects_bad_files_before_device_work(lib, tmp_path, bad):
     s = lib._lib.tgf_load(str(path).encode(), 0, lat, len(lat), ptr, 2 * ptr, 1 << 20, None, None, None, None)
     assert s == want
     assert len(lib._lib.tgf_last_error()) > 0
+
+
+def test_check_errors_needs_a_self_checking_build(lib):
+    b = C.c_uint(7)
+    assert lib._lib.tgf_check_errors(C.byref(b)) == lib.TGF_EINVAL
+    assert b.value == 0
+    assert b"TGF_CHECK" in lib._lib.tgf_last_error()
