@@ -47,6 +47,9 @@ WORKLOADS = {
     "mixed256": dict(l=[4, 6, 8], n=256, amp=None, c=0.3,
                      desc="256 x SU(3) mixed l in {4,6,8} (l x l x 3l x 3l), twist n01=1, amp U[0.2,0.6], RK3 eps=0.01 "
                           "to t=c^2 l^2/8 each"),
+    "l16x4_paper": dict(l=[16], n=4, amp=0.4, c=0.3, long=True,
+                        desc="4 x SU(3) 16x16x48x48, twist n01=1, links exp(i 0.4 omega T) seeds 0-3, RK3 eps=0.01 to "
+                             "the coupling's own scale sqrt(8t)=0.3*3l, t=25.92 (2592 steps), E/Q/P every step"),
     "l8x16_paper": dict(l=[8], n=16, amp=0.3, c=0.3, long=True,
                         desc="16 x SU(3) 8x8x24x24, twist n01=1, links exp(i 0.3 omega T) seeds 0-15, RK3 eps=0.01 to "
                              "the coupling's own scale sqrt(8t)=0.3*3l, t=6.48 (648 steps), E/Q/P every step"),
