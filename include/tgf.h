@@ -9,9 +9,11 @@
  * and the average twisted plaquette.  Host helpers give the lattice
  * normalisation N(c, Lt) (eq. latt_norm) and lambda_TGF (eq. lambdat_latt).
  *
- * Memory.  The library allocates no device memory.  Every device buffer is
- * owned by the caller (for example a torch tensor) and passed as a plain
- * pointer; sizes come from the tgf_*_bytes queries.  Device pointers must be
+ * Memory.  The stateless calls allocate no device memory.  Every device buffer
+ * is owned by the caller (for example a torch tensor) and passed as a plain
+ * pointer; sizes come from the tgf_*_bytes queries.  Only the context calls
+ * (tgf_create and the tgf_ctx_* family) allocate, and they own what they
+ * allocate.  Device pointers must be
  * 256-byte aligned (cudaMalloc and torch allocations are).  Host pointers are
  * read or written only during the call unless stated otherwise.
  *
@@ -22,13 +24,34 @@
  * Errors.  Every call returns a tgf_status; nothing is thrown across the ABI.
  * On failure tgf_last_error() returns a message (thread-local, valid until the
  * next failing call on the same thread).  Invalid arguments are rejected before
- * any device work is enqueued.
+ * any device work is enqueued.  Kernels never wait on a flag, a peer or a
+ * timer, so no call can time out; a record that comes out non-finite (NaN or
+ * infinite links, or an overflow) is noted in a device word that TGF_SYNC calls
+ * and tgf_kernel_status() turn into TGF_EKERNEL.
+ *
+ * Fault injection (tests of error handling; nothing faults on the GPU): the
+ * environment variable TGF_FAULT, read at every call, makes tgf_create fail
+ * with TGF_ENOMEM before allocating (=alloc), makes tgf_upload and
+ * tgf_set_links plant a NaN in the device copy of the first real they upload
+ * (=nan; the caller's buffer is untouched), or makes the argument checks of
+ * tgf_stage, tgf_measure, tgf_measure_slices and tgf_flow fail with TGF_EINVAL
+ * (=badarg).
+ *
+ * Threading and device state.  Calls on different streams, or from different
+ * host threads, share no mutable state except the cache of captured flow
+ * graphs (guarded by a lock), the device word of non-finite records (one per
+ * device) and tgf_measure_noalloc's fixed array (one per device).  The graph
+ * cache and that array's address are per CUDA context: after cudaDeviceReset
+ * the library must not be used again in the same process.
  *
  * Lattices.  A batch is `ncfg` (1..TGF_MAX_CFG) configurations, each with its
  * own tgf_lattice: extents L[0..3] (x0 fastest; directions 0, 1 are the short
- * twisted plane of the l x l x 3l x 3l box, 2, 3 the long periodic ones; every
- * extent >= 2) and the antisymmetric twist tensor n_{mu nu} mod 3 given by its
- * six upper entries.  The centre factor Z_{mu nu}(n) = exp(2 pi i n_{mu nu}/3)
+ * twisted plane of the l x l x 3l x 3l box, 2, 3 the long periodic ones) and
+ * the antisymmetric twist tensor n_{mu nu} mod 3 given by its six upper
+ * entries.  The extents must be the paper's box (l, l, 3l, 3l) (Sec. 3.1; for
+ * the SU(N) calls (l, l, Nl, Nl)), else the call returns TGF_EINVAL, unless the
+ * configuration's flags hold TGF_ANY_EXTENTS, which admits any extents >= 2
+ * (tests of ragged and odd boxes).  The centre factor Z_{mu nu}(n) = exp(2 pi i n_{mu nu}/3)
  * sits on the plaquettes whose corner has x_mu = x_nu = 0 (the 0-based reading
  * of the paper's x_1 = x_2 = 1) and is 1 elsewhere.
  *
@@ -56,8 +79,9 @@ extern "C" {
 typedef enum {
     TGF_OK = 0,
     TGF_EINVAL = 1,   /* bad argument: extents, twist, sizes, pointers, eps, t_end   */
+    TGF_ENOMEM = 2,   /* tgf_create could not allocate its device memory              */
     TGF_ECUDA = 3,    /* a CUDA runtime call failed (message in tgf_last_error)      */
-    TGF_EKERNEL = 4,  /* reserved: kernels report no status (non-finite inputs give NaN records) */
+    TGF_EKERNEL = 4,  /* a measured record is not finite (TGF_SYNC calls, tgf_kernel_status) */
     TGF_ESTATE = 6,   /* no configuration survived the |Q| < 1/2 cut                  */
     TGF_EIO = 7       /* checkpoint file missing, unreadable, truncated or corrupted  */
 } tgf_status;
@@ -73,6 +97,9 @@ typedef enum {
 /* Flags of tgf_measure / tgf_flow. */
 #define TGF_CLOVER_TRACELESS 1u   /* subtract tr(G)/3 from the clover G (eq. gmunu has no projection) */
 #define TGF_NO_GRAPH 2u           /* tgf_flow: launch kernels directly instead of one CUDA graph      */
+#define TGF_SYNC 4u               /* tgf_measure / tgf_flow: synchronise `stream`, then return
+                                     TGF_EKERNEL if a record written on this device since the last
+                                     such check is not finite                                       */
 /* Launch tuning of tgf_flow (results are bitwise the same for every setting; the tuner of the
  * Python package times them per workload): TGF_TUNE_GRID(k), k = 1..15, launches the stage
  * kernels as a persistent grid of k x (number of SMs) x (resident blocks per SM: 4 in FP32,
@@ -82,9 +109,13 @@ typedef enum {
 #define TGF_TUNE_SIZE_ORDER (1u << 12)
 
 typedef struct {
-    int L[4];      /* extents, x0 fastest                                          */
-    int twist[6];  /* n_01, n_02, n_03, n_12, n_13, n_23 (any integers, taken mod 3) */
+    int L[4];        /* extents, x0 fastest                                          */
+    int twist[6];    /* n_01, n_02, n_03, n_12, n_13, n_23 (any integers, taken mod 3) */
+    unsigned flags;  /* 0, or TGF_ANY_EXTENTS                                        */
 } tgf_lattice;
+
+/* tgf_lattice.flags: accept any extents >= 2 instead of only the box (l, l, 3l, 3l). */
+#define TGF_ANY_EXTENTS 1u
 
 /* One measurement of one configuration (Sec. 3.1).
  *   t  flow time
@@ -147,6 +178,11 @@ tgf_status tgf_measure(int prec, const tgf_lattice *lat, int ncfg, const void *l
                        double *scratch, size_t scratch_bytes, tgf_obs *obs_dev, size_t obs_stride,
                        int rec, double t, unsigned flags, void *stream);
 
+/* Synchronise `stream`, then return TGF_EKERNEL (with the configuration and record in the
+ * message) if a record written on the current device since the last check is not finite, and
+ * clear the note.  The paper has no counterpart: this is the library's failure report. */
+tgf_status tgf_kernel_status(void *stream);
+
 /* tgf_measure for callers that cannot allocate device memory: the same measurement, with the
  * scratch held in a fixed device array inside the library instead of a caller buffer.  The
  * paper has no counterpart; it serves code that may not call cudaMalloc, such as a plug-in
@@ -157,8 +193,11 @@ tgf_status tgf_measure(int prec, const tgf_lattice *lat, int ncfg, const void *l
  * until the process exits; a batch whose tgf_scratch_bytes exceeds it is rejected with
  * TGF_EINVAL and a message (about 41,000 sites in FP64, 82,000 in FP32 forms).
  * Set-up: the first call on each device looks up the array's device address with
- * cudaGetSymbolAddress (that device must be current); make that first call before any stream
- * capture.  No call allocates or frees device memory.  All calls share the one array, which
+ * cudaGetSymbolAddress (that device must be current) and keeps it for the process; that first
+ * call may also load the library's device code and commit the 36 MiB, so make it during set-up,
+ * before any stream capture and outside latency-critical loops.  The kept address belongs to
+ * the device's CUDA context: after cudaDeviceReset the call must not be used again.  No call of
+ * tgf_measure_noalloc allocates or frees device memory.  All calls share the one array, which
  * keeps the last call's contents; each call overwrites everything it reads, so nothing needs
  * clearing, but calls whose kernels may overlap on the GPU (unordered streams) race. */
 tgf_status tgf_measure_noalloc(int prec, const tgf_lattice *lat, int ncfg, const void *links,
@@ -190,6 +229,40 @@ tgf_status tgf_flow(int prec, const tgf_lattice *lat, int ncfg, void *w, void *w
 
 /* Number of records tgf_flow writes for one configuration (host arithmetic only). */
 tgf_status tgf_flow_records(double eps, double t_end, int measure_every, int *n_records);
+
+/* ---- library-owned context --------------------------------------------------------------- */
+
+/* The stateful form of the calls above, for callers that want the library to own the device
+ * memory: a context holds one batch (its lattices, precision, re-projection period and flags)
+ * with its links, ping-pong buffer, accumulator, scratch, staging and records on one device.
+ * Every call makes that device current and restores the caller's current device afterwards.
+ * A context is not thread-safe; separate contexts are independent.
+ *
+ * tgf_create: validates as the stateless calls do and allocates everything (links zeroed);
+ *   TGF_ENOMEM if cudaMalloc runs out of memory (nothing is left allocated), TGF_EINVAL for
+ *   bad arguments or an unknown device.  flags: TGF_CLOVER_TRACELESS, TGF_NO_GRAPH.
+ * tgf_destroy: frees everything (NULL is accepted).
+ * tgf_set_links / tgf_get_links: configuration `cfg` from / to a host canonical buffer of
+ *   exactly V * 72 doubles (synchronous).  tgf_set_links_device: from a device canonical buffer,
+ *   enqueued on `stream`.
+ * tgf_ctx_measure: {t, E, Q, P, S} of every configuration into out[ncfg] (host); synchronises
+ *   `stream`; TGF_EKERNEL if a record is not finite.
+ * tgf_ctx_flow: tgf_flow of the batch to t_end[c] (host array), records into out[c * cap + r]
+ *   (host, cap >= tgf_flow_records of every configuration), counts into n_written[ncfg];
+ *   synchronises `stream`; TGF_EKERNEL if a record is not finite.
+ * tgf_ctx_save / tgf_ctx_load: tgf_save / tgf_load of the context's links. */
+typedef struct tgf_ctx tgf_ctx;
+tgf_status tgf_create(tgf_ctx **out, int device, int prec, int ncfg, const tgf_lattice *lat, int reunit_every,
+                      unsigned flags);
+void tgf_destroy(tgf_ctx *ctx);
+tgf_status tgf_set_links(tgf_ctx *ctx, int cfg, const double *host_canon, size_t n_doubles);
+tgf_status tgf_set_links_device(tgf_ctx *ctx, int cfg, const double *canon_dev, size_t n_doubles, void *stream);
+tgf_status tgf_get_links(tgf_ctx *ctx, int cfg, double *host_canon, size_t n_doubles);
+tgf_status tgf_ctx_measure(tgf_ctx *ctx, double t, tgf_obs *out, void *stream);
+tgf_status tgf_ctx_flow(tgf_ctx *ctx, double eps, const double *t_end, int measure_every, tgf_obs *out, size_t cap,
+                        int *n_written, void *stream);
+tgf_status tgf_ctx_save(tgf_ctx *ctx, const char *path, double t, long long step, unsigned long long seed);
+tgf_status tgf_ctx_load(tgf_ctx *ctx, const char *path, double *t, long long *step, unsigned long long *seed);
 
 /* ---- SU(N) forms (FP64; Sec. 1, Sec. 3.1 with N colours, Sec. 5) ---------------------------- */
 
@@ -296,10 +369,15 @@ tgf_status tgf_slice_correlator(const double *q, size_t q_stride, const double *
 /* ---- diagnostics ---------------------------------------------------------------------------- */
 
 /* FMA-pipe peak of the current device in TFLOP/s (2 flops per FMA) for TGF_FP64 or TGF_FP32:
- * the roofline denominator of the flow kernels, which are bound by vector FP arithmetic.  The
+ * the roofline denominator of the flow kernels, which are bound by vector FP arithmetic.  With
+ * TGF_FMA_PEAK_FP32X2 the same chains run as packed fma.rn.f32x2 pairs, with
+ * TGF_FMA_PEAK_FP32_MIXED as packed and scalar FMAs interleaved: the FP32 flow kernels use
+ * packed pairs, so these check that no mix of the two forms exceeds the scalar FP32 peak.  The
  * paper has no counterpart; this is a measurement aid.  `sink_dev` is a caller-owned device
  * buffer of at least blocks_per_sm * (number of SMs) * 8 bytes that the kernel may write;
  * the call synchronises `stream`. */
+#define TGF_FMA_PEAK_FP32X2 3
+#define TGF_FMA_PEAK_FP32_MIXED 4
 tgf_status tgf_fma_peak(int prec, void *sink_dev, int blocks_per_sm, int iters, double *tflops,
                         void *stream);
 

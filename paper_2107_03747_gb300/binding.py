@@ -16,11 +16,14 @@ PKG = os.path.dirname(os.path.abspath(__file__))
 # TGF_LIB_PATH selects another build of the same library (kernel-variant sweeps of the tuner)
 LIB_PATH = os.environ.get("TGF_LIB_PATH", os.path.join(PKG, "libtgf.so"))
 
-TGF_OK, TGF_EINVAL, TGF_ECUDA, TGF_EKERNEL, TGF_ESTATE, TGF_EIO = 0, 1, 3, 4, 6, 7
+TGF_OK, TGF_EINVAL, TGF_ENOMEM, TGF_ECUDA, TGF_EKERNEL, TGF_ESTATE, TGF_EIO = 0, 1, 2, 3, 4, 6, 7
 TGF_FP64, TGF_FP32, TGF_FP32_R12 = 0, 1, 2
 TGF_CLOVER_TRACELESS = 1
 TGF_NO_GRAPH = 2
+TGF_SYNC = 4
+TGF_ANY_EXTENTS = 1
 TGF_MAX_CFG = 256
+TGF_FMA_PEAK_FP32X2, TGF_FMA_PEAK_FP32_MIXED = 3, 4
 PRECISIONS = {"fp64": TGF_FP64, "fp32": TGF_FP32, "fp32_r12": TGF_FP32_R12}
 
 
@@ -31,7 +34,7 @@ class TgfError(RuntimeError):
 
 
 class tgf_lattice(C.Structure):
-    _fields_ = [("L", C.c_int * 4), ("twist", C.c_int * 6)]
+    _fields_ = [("L", C.c_int * 4), ("twist", C.c_int * 6), ("flags", C.c_uint)]
 
 
 class tgf_obs(C.Structure):
@@ -75,6 +78,15 @@ _SIGS = {
     "tgf_load": [C.c_char_p, C.c_int, _LATP, C.c_int, _P, _P, _SZ, C.POINTER(C.c_double), C.POINTER(C.c_longlong),
                  C.POINTER(C.c_ulonglong), _P],
     "tgf_check_errors": [C.POINTER(C.c_uint)],
+    "tgf_kernel_status": [_P],
+    "tgf_create": [C.POINTER(C.c_void_p), C.c_int, C.c_int, C.c_int, _LATP, C.c_int, C.c_uint],
+    "tgf_set_links": [C.c_void_p, C.c_int, _P, _SZ],
+    "tgf_set_links_device": [C.c_void_p, C.c_int, _P, _SZ, _P],
+    "tgf_get_links": [C.c_void_p, C.c_int, _P, _SZ],
+    "tgf_ctx_measure": [C.c_void_p, C.c_double, _P, _P],
+    "tgf_ctx_flow": [C.c_void_p, C.c_double, C.POINTER(C.c_double), C.c_int, _P, _SZ, C.POINTER(C.c_int), _P],
+    "tgf_ctx_save": [C.c_void_p, C.c_char_p, C.c_double, C.c_longlong, C.c_ulonglong],
+    "tgf_ctx_load": [C.c_void_p, C.c_char_p, C.POINTER(C.c_double), C.POINTER(C.c_longlong), C.POINTER(C.c_ulonglong)],
     "tgf_norm": [C.c_double, C.c_int, C.c_int, C.POINTER(C.c_double)],
     "tgf_fma_peak": [C.c_int, _P, C.c_int, C.c_int, C.POINTER(C.c_double), _P],
     "tgf_lambda": [C.c_double, C.c_int, C.c_double, C.POINTER(C.c_double), C.POINTER(C.c_double), C.c_int,
@@ -92,8 +104,10 @@ _lib.tgf_status_string.restype = C.c_char_p
 _lib.tgf_status_string.argtypes = [C.c_int]
 _lib.tgf_version.restype = C.c_char_p
 _lib.tgf_version.argtypes = []
+_lib.tgf_destroy.restype = None
+_lib.tgf_destroy.argtypes = [C.c_void_p]
 
-EXPORTED = sorted(list(_SIGS) + ["tgf_last_error", "tgf_status_string", "tgf_version", "tgf_crc32"])
+EXPORTED = sorted(list(_SIGS) + ["tgf_last_error", "tgf_status_string", "tgf_version", "tgf_crc32", "tgf_destroy"])
 
 
 def _check(status: int):
@@ -117,14 +131,18 @@ def _stream(stream):
     return stream.cuda_stream
 
 
-def lattices(Ls, twists=None):
-    """ctypes array of tgf_lattice from extents (L0, L1, L2, L3) and twist 6-tuples (default n_01 = 1)."""
+def lattices(Ls, twists=None, any_extents=False):
+    """ctypes array of tgf_lattice from extents (L0, L1, L2, L3) and twist 6-tuples (default n_01 = 1).
+
+    The library accepts only the paper's box (l, l, 3l, 3l) (SU(N): (l, l, Nl, Nl)) unless
+    `any_extents` sets TGF_ANY_EXTENTS."""
     n = len(Ls)
     arr = (tgf_lattice * n)()
     for i, L in enumerate(Ls):
         arr[i].L[:] = [int(x) for x in L]
         tw = (1, 0, 0, 0, 0, 0) if twists is None else twists[i]
         arr[i].twist[:] = [int(x) for x in tw]
+        arr[i].flags = TGF_ANY_EXTENTS if any_extents else 0
     return arr
 
 
@@ -268,11 +286,11 @@ def _sun_size(fn, N, lat) -> int:
 class SunBatch:
     """SU(N) configurations (FP64) with their device buffers: links, the ping-pong buffer, X, scratch."""
 
-    def __init__(self, N, Ls, twists=None, device="cuda"):
+    def __init__(self, N, Ls, twists=None, device="cuda", any_extents=False):
         import torch
 
         self.N, self.Ls, self.device = N, [tuple(L) for L in Ls], device
-        self.lat = lattices(self.Ls, twists)
+        self.lat = lattices(self.Ls, twists, any_extents)
         nb = _sun_size(_lib.tgf_sun_links_bytes, N, self.lat)
         self.links = torch.empty(nb, dtype=torch.uint8, device=device)
         self.links_tmp = torch.empty(nb, dtype=torch.uint8, device=device)
@@ -320,6 +338,11 @@ class SunBatch:
         _check(_lib.tgf_sun_measure(self.N, self.lat, n, _ptr(self.links), _ptr(self.scratch),
                                     self.scratch.numel(), _ptr(obs), 1, 0, t, flags, _stream(stream)))
         return obs.cpu().numpy().reshape(n, 5)
+
+
+def tgf_kernel_status(stream=None):
+    """Synchronise `stream`; raises TgfError(TGF_EKERNEL) if a record came out non-finite since the last check."""
+    _check(_lib.tgf_kernel_status(_stream(stream)))
 
 
 def tgf_check_errors() -> int:
@@ -380,11 +403,11 @@ class FlowBatch:
     ``scratch`` the measurement partials.  All are torch uint8 tensors on ``device``.
     """
 
-    def __init__(self, Ls, prec="fp64", twists=None, device="cuda"):
+    def __init__(self, Ls, prec="fp64", twists=None, device="cuda", any_extents=False):
         import torch
 
         self.prec = PRECISIONS[prec] if isinstance(prec, str) else int(prec)
-        self.lat = lattices(Ls, twists)
+        self.lat = lattices(Ls, twists, any_extents)
         self.Ls = [tuple(int(x) for x in L) for L in Ls]
         self.device = torch.device(device)
         nb = tgf_links_bytes(self.prec, self.lat)
@@ -464,3 +487,62 @@ class FlowBatch:
         nrec = tgf_flow(self.prec, self.lat, self.links, self.links_tmp, self.accum, self.scratch, eps, te, obs,
                         cap, measure_every, reunit_every, flags, stream)
         return obs[: self.ncfg * cap * 5].view(self.ncfg, cap, 5), nrec
+
+
+class Context:
+    """The library-owned context (tgf_create ... tgf_destroy): the library allocates and owns the
+    batch's device memory; fields go in and out as canonical complex128 numpy arrays."""
+
+    def __init__(self, Ls, prec="fp64", twists=None, device=0, reunit_every=0, flags=0, any_extents=False):
+        self.prec = PRECISIONS[prec] if isinstance(prec, str) else int(prec)
+        self.Ls = [tuple(int(x) for x in L) for L in Ls]
+        self.lat = lattices(self.Ls, twists, any_extents)
+        self._h = C.c_void_p()
+        _check(_lib.tgf_create(C.byref(self._h), int(device), self.prec, len(self.Ls), self.lat, int(reunit_every),
+                               int(flags)))
+
+    def close(self):
+        if self._h:
+            _lib.tgf_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_links(self, cfg, field):
+        f = np.ascontiguousarray(field, dtype=np.complex128)
+        _check(_lib.tgf_set_links(self._h, int(cfg), f.ctypes.data, f.size * 2))
+
+    def get_links(self, cfg):
+        L = self.Ls[cfg]
+        out = np.empty((L[3], L[2], L[1], L[0], 4, 3, 3), dtype=np.complex128)
+        _check(_lib.tgf_get_links(self._h, int(cfg), out.ctypes.data, out.size * 2))
+        return out
+
+    def measure(self, t=0.0, stream=None):
+        out = (tgf_obs * len(self.Ls))()
+        _check(_lib.tgf_ctx_measure(self._h, float(t), C.addressof(out), _stream(stream)))
+        return np.array([[o.t, o.E, o.Q, o.P, o.S] for o in out])
+
+    def flow(self, eps, t_end, measure_every=1, stream=None):
+        """Records as an (ncfg, cap, 5) numpy array and the count per configuration."""
+        n = len(self.Ls)
+        te = [float(t_end)] * n if np.isscalar(t_end) else [float(x) for x in t_end]
+        cap = max(tgf_flow_records(eps, t, measure_every) for t in te)
+        out = (tgf_obs * (n * cap))()
+        nw = (C.c_int * n)()
+        _check(_lib.tgf_ctx_flow(self._h, float(eps), (C.c_double * n)(*te), int(measure_every), C.addressof(out), cap,
+                                 nw, _stream(stream)))
+        rec = np.array([[o.t, o.E, o.Q, o.P, o.S] for o in out]).reshape(n, cap, 5)
+        return rec, list(nw)
+
+    def save(self, path, t, step, seed):
+        _check(_lib.tgf_ctx_save(self._h, str(path).encode(), float(t), int(step), int(seed) & 0xFFFFFFFFFFFFFFFF))
+
+    def load(self, path):
+        t, step, seed = C.c_double(), C.c_longlong(), C.c_ulonglong()
+        _check(_lib.tgf_ctx_load(self._h, str(path).encode(), C.byref(t), C.byref(step), C.byref(seed)))
+        return t.value, step.value, seed.value

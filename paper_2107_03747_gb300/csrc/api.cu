@@ -7,8 +7,11 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <limits>
 #include <list>
+#include <memory>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -75,16 +78,56 @@ tgf_status check_prec(int prec) {
     return TGF_OK;
 }
 
-tgf_status check_lat(const tgf_lattice* lat, int ncfg) {
+// Extents, size limits and the box of the paper (Sec. 3.1): L = (l, l, N l, N l) with the twisted
+// plane first, unless the configuration sets TGF_ANY_EXTENTS.
+tgf_status check_lat(const tgf_lattice* lat, int ncfg, int N = 3) {
     if (!lat) return fail(TGF_EINVAL, "lattice array is NULL");
     if (ncfg < 1 || ncfg > TGF_MAX_CFG) return fail(TGF_EINVAL, "ncfg = %d outside 1..%d", ncfg, TGF_MAX_CFG);
     for (int c = 0; c < ncfg; ++c) {
+        const int* L = lat[c].L;
         for (int mu = 0; mu < 4; ++mu)
-            if (lat[c].L[mu] < 2 || lat[c].L[mu] > 4096)
-                return fail(TGF_EINVAL, "configuration %d: extent L[%d] = %d outside 2..4096", c, mu, lat[c].L[mu]);
+            if (L[mu] < 2 || L[mu] > 4096)
+                return fail(TGF_EINVAL, "configuration %d: extent L[%d] = %d outside 2..4096", c, mu, L[mu]);
         if (sites(lat[c]) > (int64_t(1) << 28))
             return fail(TGF_EINVAL, "configuration %d: %lld sites exceed 2^28", c, (long long)sites(lat[c]));
+        if (lat[c].flags & ~TGF_ANY_EXTENTS)
+            return fail(TGF_EINVAL, "configuration %d: unknown lattice flags 0x%x", c, lat[c].flags);
+        if (!(lat[c].flags & TGF_ANY_EXTENTS) && (L[1] != L[0] || L[2] != N * L[0] || L[3] != N * L[0]))
+            return fail(TGF_EINVAL,
+                        "configuration %d: extents %dx%dx%dx%d are not the twisted box l x l x %dl x %dl "
+                        "(set TGF_ANY_EXTENTS in the lattice's flags to allow other extents)",
+                        c, L[0], L[1], L[2], L[3], N, N);
     }
+    return TGF_OK;
+}
+
+// ---- host-side fault injection (TGF_FAULT) ---------------------------------------------------
+// TGF_FAULT=alloc: tgf_create fails as if cudaMalloc had (TGF_ENOMEM), allocating nothing;
+// TGF_FAULT=nan: tgf_upload and tgf_set_links plant a NaN in the first real of the first
+// configuration they copy (in the device staging copy; the caller's buffer is untouched);
+// TGF_FAULT=badarg: the argument checks of the hot-path calls fail (TGF_EINVAL).
+// Read at every call, so a test can set and clear it in-process.  Nothing faults on the GPU.
+bool fault_is(const char* what) {
+    const char* v = std::getenv("TGF_FAULT");
+    return v && std::strcmp(v, what) == 0;
+}
+
+// TGF_EKERNEL if a record written since the last read on this device came out non-finite
+// (synchronises `st`); `stride` decodes the slot into configuration and record.
+tgf_status check_nonfinite(cudaStream_t st, size_t stride, const char* call) {
+    cudaError_t e = cudaSuccess;
+    const unsigned long long v = nonfinite_read_and_clear(st, &e);
+    if (e != cudaSuccess) return fail(TGF_ECUDA, "%s: reading the kernel status: %s", call, cudaGetErrorString(e));
+    if (v) {
+        const unsigned long long slot = v - 1, sd = stride ? stride : 1;
+        return fail(TGF_EKERNEL, "%s: the record of configuration %llu, record %llu (observable slot %llu) is not finite "
+                    "(non-finite links or an overflow)", call, slot / sd, slot % sd, slot);
+    }
+    return TGF_OK;
+}
+
+tgf_status injected_badarg(const char* call) {
+    if (fault_is("badarg")) return fail(TGF_EINVAL, "%s: argument check failed (fault injected by TGF_FAULT=badarg)", call);
     return TGF_OK;
 }
 
@@ -142,13 +185,9 @@ Batch make_batch(const tgf_lattice* lat, const Layout& Ly, const std::vector<int
     for (int i = 0; i < B.ncfg; ++i) {
         const int c = which[i];
         CfgDesc& d = B.c[i];
-        for (int mu = 0; mu < 4; ++mu) d.L[mu] = lat[c].L[mu];
-        d.st[0] = 1;
-        for (int mu = 1; mu < 4; ++mu) d.st[mu] = d.st[mu - 1] * d.L[mu - 1];
-        d.V = (int)sites(lat[c]);
+        set_geometry(d, lat[c].L);
         d.Vp = (int)padded(d.V);
         d.blk0 = blk;
-        d.rec = 0;
         d.w_off = Ly.w_off[c];
         d.x_off = Ly.x_off[c];
         d.m_off = Ly.m_off[c];
@@ -181,7 +220,6 @@ tgf_status enqueue_sum(int prec, unsigned flags, const tgf_lattice* lat, const L
                        size_t obs_stride, double* scratch, tgf_obs* obs, cudaStream_t st) {
     Batch B = make_batch(lat, Ly, which, kMeasureSites);
     for (int i = 0; i < B.ncfg; ++i) {
-        B.c[i].rec = rec[i];
         B.c[i].h = t[i];
         B.c[i].o_off = (int64_t)which[i] * (int64_t)obs_stride + rec[i];
     }
@@ -234,28 +272,27 @@ cudaStream_t g_capture[64] = {};
 
 // Side branch of a flow: the clover sum + reduction of a measured step (HBM-bound) runs on this
 // stream while stages 2 and 3 (FP-pipe-bound) run on the main one; captured into the same graph
-// as parallel nodes.
+// as parallel nodes.  Every enqueue_flow call creates its own stream and events and releases them
+// when it returns (CUDA releases them once the enqueued work is done), so flows enqueued at the
+// same time from several host threads never share a fork or join event.
 struct SideBranch {
     cudaStream_t s = nullptr;
     cudaEvent_t fork = nullptr, join = nullptr;
-};
-SideBranch g_side[64];
-std::mutex g_side_mu;
-
-tgf_status side_branch(SideBranch*& out) {
-    int dev = 0;
-    TGF_CUDA(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= 64) return fail(TGF_EINVAL, "device %d out of range", dev);
-    std::lock_guard<std::mutex> lk(g_side_mu);
-    SideBranch& sb = g_side[dev];
-    if (!sb.s) {
-        TGF_CUDA(cudaStreamCreateWithFlags(&sb.s, cudaStreamNonBlocking));
-        TGF_CUDA(cudaEventCreateWithFlags(&sb.fork, cudaEventDisableTiming));
-        TGF_CUDA(cudaEventCreateWithFlags(&sb.join, cudaEventDisableTiming));
+    SideBranch() = default;
+    SideBranch(const SideBranch&) = delete;
+    SideBranch& operator=(const SideBranch&) = delete;
+    ~SideBranch() {
+        if (fork) cudaEventDestroy(fork);
+        if (join) cudaEventDestroy(join);
+        if (s) cudaStreamDestroy(s);
     }
-    out = &sb;
-    return TGF_OK;
-}
+    tgf_status create() {
+        TGF_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+        TGF_CUDA(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
+        TGF_CUDA(cudaEventCreateWithFlags(&join, cudaEventDisableTiming));
+        return TGF_OK;
+    }
+};
 
 }  // namespace
 
@@ -267,15 +304,16 @@ const char* tgf_status_string(int status) {
     switch (status) {
         case TGF_OK: return "ok";
         case TGF_EINVAL: return "invalid argument";
+        case TGF_ENOMEM: return "out of device memory";
         case TGF_ECUDA: return "CUDA error";
-        case TGF_EKERNEL: return "kernel error";
+        case TGF_EKERNEL: return "non-finite result";
         case TGF_ESTATE: return "no configuration kept";
         case TGF_EIO: return "checkpoint file error";
         default: return "unknown status";
     }
 }
 
-const char* tgf_version(void) { return "1.0.0"; }
+const char* tgf_version(void) { return "1.1.0"; }
 
 tgf_status tgf_links_bytes(int prec, const tgf_lattice* lat, int ncfg, size_t* bytes) {
     tgf_status s;
@@ -354,9 +392,13 @@ tgf_status tgf_upload(int prec, const tgf_lattice* lat, int ncfg, const double* 
     if (!canon_host) return fail(TGF_EINVAL, "canon_host is NULL");
     cudaStream_t st = (cudaStream_t)stream;
     Layout Ly = layout(prec, lat, ncfg);
+    static const double kNaN = std::numeric_limits<double>::quiet_NaN();
+    const bool plant_nan = fault_is("nan");
     for (int c = 0; c < ncfg; ++c) {
         TGF_CUDA(cudaMemcpyAsync(staging_dev, canon_host + Ly.c_off[c], (size_t)sites(lat[c]) * 72 * sizeof(double),
                                  cudaMemcpyHostToDevice, st));
+        if (plant_nan && c == 0)
+            TGF_CUDA(cudaMemcpyAsync(staging_dev, &kNaN, sizeof kNaN, cudaMemcpyHostToDevice, st));
         Batch B = make_batch(lat, Ly, std::vector<int>{c}, 32);
         B.c[0].x_off = 0;
         launch_pack(prec, B, staging_dev, links, st);
@@ -391,6 +433,7 @@ tgf_status tgf_stage(int prec, const tgf_lattice* lat, int ncfg, const void* w_i
                      double eps, int reunit, void* stream) {
     Range range_("tgf_stage");
     tgf_status s;
+    if ((s = injected_badarg("tgf_stage"))) return s;
     if ((s = check_prec(prec)) || (s = check_lat(lat, ncfg)) || (s = check_ptr(w_in, "w_in")) ||
         (s = check_ptr(w_out, "w_out")) || (s = check_ptr(accum, "accum")))
         return s;
@@ -409,6 +452,7 @@ tgf_status tgf_measure(int prec, const tgf_lattice* lat, int ncfg, const void* l
                        void* stream) {
     Range range_("tgf_measure");
     tgf_status s;
+    if ((s = injected_badarg("tgf_measure"))) return s;
     if ((s = check_prec(prec)) || (s = check_lat(lat, ncfg)) || (s = check_ptr(links, "links")) ||
         (s = check_ptr(scratch, "scratch")) || (s = check_ptr(obs_dev, "obs_dev")))
         return s;
@@ -417,10 +461,19 @@ tgf_status tgf_measure(int prec, const tgf_lattice* lat, int ncfg, const void* l
         return fail(TGF_EINVAL, "scratch of %zu bytes too small (need %zu)", scratch_bytes, Ly.scratch_bytes(prec));
     if (rec < 0 || (ncfg > 1 && (size_t)rec >= obs_stride))
         return fail(TGF_EINVAL, "record %d outside the stride %zu", rec, obs_stride);
+    if (flags & ~(TGF_CLOVER_TRACELESS | TGF_SYNC)) return fail(TGF_EINVAL, "tgf_measure: unknown flags 0x%x", flags);
     std::vector<int> which = all_cfgs(ncfg), recs(ncfg, rec);
     std::vector<double> ts(ncfg, t);
-    return enqueue_measure(prec, flags, lat, Ly, which, recs, ts, obs_stride, links, scratch, obs_dev,
-                           (cudaStream_t)stream);
+    if ((s = enqueue_measure(prec, flags, lat, Ly, which, recs, ts, obs_stride, links, scratch, obs_dev,
+                             (cudaStream_t)stream)))
+        return s;
+    if (flags & TGF_SYNC) return check_nonfinite((cudaStream_t)stream, obs_stride, "tgf_measure");
+    return TGF_OK;
+}
+
+tgf_status tgf_kernel_status(void* stream) {
+    Range range_("tgf_kernel_status");
+    return check_nonfinite((cudaStream_t)stream, 0, "tgf_kernel_status");
 }
 
 // ---- self-checking builds ------------------------------------------------------------------
@@ -593,13 +646,9 @@ Batch make_sun_batch(int N, const tgf_lattice* lat, int ncfg, int spb) {
     int64_t w = 0, x = 0, cc = 0;
     for (int c = 0; c < ncfg; ++c) {
         CfgDesc& d = B.c[c];
-        for (int mu = 0; mu < 4; ++mu) d.L[mu] = lat[c].L[mu];
-        d.st[0] = 1;
-        for (int mu = 1; mu < 4; ++mu) d.st[mu] = d.st[mu - 1] * d.L[mu - 1];
-        d.V = (int)sites(lat[c]);
+        set_geometry(d, lat[c].L);
         d.Vp = (int)padded(d.V);
         d.blk0 = blk;
-        d.rec = 0;
         d.w_off = w;
         d.x_off = x;
         d.m_off = cc;
@@ -631,7 +680,7 @@ size_t sun_scratch(const tgf_lattice* lat, int ncfg) {
 
 tgf_status tgf_sun_links_bytes(int N, const tgf_lattice* lat, int ncfg, size_t* bytes) {
     tgf_status s;
-    if ((s = check_n(N)) || (s = check_lat(lat, ncfg))) return s;
+    if ((s = check_n(N)) || (s = check_lat(lat, ncfg, N))) return s;
     if (!bytes) return fail(TGF_EINVAL, "bytes is NULL");
     size_t b = 0;
     for (int c = 0; c < ncfg; ++c) b += (size_t)4 * N * N * 16 * (size_t)padded(sites(lat[c]));
@@ -641,7 +690,7 @@ tgf_status tgf_sun_links_bytes(int N, const tgf_lattice* lat, int ncfg, size_t* 
 
 tgf_status tgf_sun_accum_bytes(int N, const tgf_lattice* lat, int ncfg, size_t* bytes) {
     tgf_status s;
-    if ((s = check_n(N)) || (s = check_lat(lat, ncfg))) return s;
+    if ((s = check_n(N)) || (s = check_lat(lat, ncfg, N))) return s;
     if (!bytes) return fail(TGF_EINVAL, "bytes is NULL");
     size_t b = 0;
     for (int c = 0; c < ncfg; ++c) b += (size_t)4 * N * N * 8 * (size_t)padded(sites(lat[c]));
@@ -651,7 +700,7 @@ tgf_status tgf_sun_accum_bytes(int N, const tgf_lattice* lat, int ncfg, size_t* 
 
 tgf_status tgf_sun_scratch_bytes(int N, const tgf_lattice* lat, int ncfg, size_t* bytes) {
     tgf_status s;
-    if ((s = check_n(N)) || (s = check_lat(lat, ncfg))) return s;
+    if ((s = check_n(N)) || (s = check_lat(lat, ncfg, N))) return s;
     if (!bytes) return fail(TGF_EINVAL, "bytes is NULL");
     *bytes = sun_scratch(lat, ncfg);
     return TGF_OK;
@@ -659,7 +708,7 @@ tgf_status tgf_sun_scratch_bytes(int N, const tgf_lattice* lat, int ncfg, size_t
 
 tgf_status tgf_sun_pack(int N, const tgf_lattice* lat, int ncfg, const double* canon_dev, void* links, void* stream) {
     tgf_status s;
-    if ((s = check_n(N)) || (s = check_lat(lat, ncfg)) || (s = check_ptr(canon_dev, "canon_dev")) ||
+    if ((s = check_n(N)) || (s = check_lat(lat, ncfg, N)) || (s = check_ptr(canon_dev, "canon_dev")) ||
         (s = check_ptr(links, "links")))
         return s;
     Batch B = make_sun_batch(N, lat, ncfg, 128);
@@ -669,7 +718,7 @@ tgf_status tgf_sun_pack(int N, const tgf_lattice* lat, int ncfg, const double* c
 
 tgf_status tgf_sun_unpack(int N, const tgf_lattice* lat, int ncfg, const void* links, double* canon_dev, void* stream) {
     tgf_status s;
-    if ((s = check_n(N)) || (s = check_lat(lat, ncfg)) || (s = check_ptr(canon_dev, "canon_dev")) ||
+    if ((s = check_n(N)) || (s = check_lat(lat, ncfg, N)) || (s = check_ptr(canon_dev, "canon_dev")) ||
         (s = check_ptr(links, "links")))
         return s;
     Batch B = make_sun_batch(N, lat, ncfg, 128);
@@ -682,7 +731,7 @@ tgf_status tgf_sun_stage(int N, const tgf_lattice* lat, int ncfg, const void* w_
                          double eps, void* stream) {
     Range range_("tgf_sun_stage");
     tgf_status s;
-    if ((s = check_n(N)) || (s = check_lat(lat, ncfg)) || (s = check_ptr(w_in, "w_in")) ||
+    if ((s = check_n(N)) || (s = check_lat(lat, ncfg, N)) || (s = check_ptr(w_in, "w_in")) ||
         (s = check_ptr(w_out, "w_out")) || (s = check_ptr(accum, "accum")))
         return s;
     if (stage < 1 || stage > 3) return fail(TGF_EINVAL, "stage %d outside 1..3", stage);
@@ -700,7 +749,7 @@ tgf_status tgf_sun_measure(int N, const tgf_lattice* lat, int ncfg, const void* 
                            void* stream) {
     Range range_("tgf_sun_measure");
     tgf_status s;
-    if ((s = check_n(N)) || (s = check_lat(lat, ncfg)) || (s = check_ptr(links, "links")) ||
+    if ((s = check_n(N)) || (s = check_lat(lat, ncfg, N)) || (s = check_ptr(links, "links")) ||
         (s = check_ptr(scratch, "scratch")) || (s = check_ptr(obs_dev, "obs_dev")))
         return s;
     if (scratch_bytes < sun_scratch(lat, ncfg))
@@ -752,6 +801,7 @@ tgf_status tgf_measure_slices(int prec, const tgf_lattice* lat, int ncfg, const 
                               void* stream) {
     Range range_("tgf_measure_slices");
     tgf_status s;
+    if ((s = injected_badarg("tgf_measure_slices"))) return s;
     if ((s = check_prec(prec)) || (s = check_lat(lat, ncfg)) || (s = check_ptr(links, "links")) ||
         (s = check_ptr(scratch, "scratch")) || (s = check_ptr(q_dev, "q_dev")))
         return s;
@@ -772,7 +822,7 @@ tgf_status tgf_measure_slices(int prec, const tgf_lattice* lat, int ncfg, const 
     int blk = 0;
     for (int c = 0; c < ncfg; ++c) {
         Q.c[c].blk0 = blk;
-        Q.c[c].rec = c;
+        Q.c[c].o_off = c;
         blk += lat[c].L[dir];
     }
     Q.nblk = blk;
@@ -816,8 +866,9 @@ static tgf_status enqueue_flow(int prec, const tgf_lattice* lat, int ncfg, const
     const bool by_size = (flags & TGF_TUNE_SIZE_ORDER) != 0;
     void* cur = w;
     void* alt = w_tmp;
-    SideBranch* sb = nullptr;
-    if ((s = side_branch(sb))) return s;
+    SideBranch side;
+    if ((s = side.create())) return s;
+    SideBranch* sb = &side;
     bool pending = false;  // a side-branch sum still reads the clover halves / writes the partials
     auto join = [&]() -> tgf_status {
         if (pending) {
@@ -896,6 +947,7 @@ tgf_status tgf_flow(int prec, const tgf_lattice* lat, int ncfg, void* w, void* w
                     unsigned flags, tgf_obs* obs_dev, size_t obs_cap, int* n_records, void* stream) {
     Range range_("tgf_flow");
     tgf_status s;
+    if ((s = injected_badarg("tgf_flow"))) return s;
     if ((s = check_prec(prec)) || (s = check_lat(lat, ncfg)) || (s = check_ptr(w, "w")) ||
         (s = check_ptr(w_tmp, "w_tmp")) || (s = check_ptr(accum, "accum")) || (s = check_ptr(scratch, "scratch")) ||
         (s = check_ptr(obs_dev, "obs_dev")))
@@ -917,9 +969,14 @@ tgf_status tgf_flow(int prec, const tgf_lattice* lat, int ncfg, void* w, void* w
         n_records[c] = nr;
     }
     cudaStream_t st = (cudaStream_t)stream;
-    if (flags & TGF_NO_GRAPH)
-        return enqueue_flow(prec, lat, ncfg, Ly, w, w_tmp, accum, scratch, eps, n, rest, measure_every, reunit_every,
-                            flags, obs_dev, obs_cap, st);
+    const bool sync = (flags & TGF_SYNC) != 0;
+    flags &= ~TGF_SYNC;
+    if (flags & TGF_NO_GRAPH) {
+        if ((s = enqueue_flow(prec, lat, ncfg, Ly, w, w_tmp, accum, scratch, eps, n, rest, measure_every, reunit_every,
+                              flags, obs_dev, obs_cap, st)))
+            return s;
+        return sync ? check_nonfinite(st, obs_cap, "tgf_flow") : TGF_OK;
+    }
 
     // ---- one CUDA graph per distinct call, cached -----------------------------------------
     int dev = 0;
@@ -966,7 +1023,241 @@ tgf_status tgf_flow(int prec, const tgf_lattice* lat, int ncfg, void* w, void* w
         }
     }
     TGF_CUDA(cudaGraphLaunch(exec, st));
+    return sync ? check_nonfinite(st, obs_cap, "tgf_flow") : TGF_OK;
+}
+
+}  // extern "C"
+
+// ---- library-owned context (the stateful form of the calls above) -------------------------------
+
+namespace {
+
+// Makes `dev` current for the lifetime of the guard and restores the caller's device after.
+struct DeviceGuard {
+    int prev = -1;
+    cudaError_t err = cudaSuccess;
+    explicit DeviceGuard(int dev) {
+        err = cudaGetDevice(&prev);
+        if (err == cudaSuccess && prev != dev) err = cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+tgf_status alloc_dev(void** p, size_t bytes, const char* what) {
+    const cudaError_t e = cudaMalloc(p, bytes < 256 ? 256 : bytes);
+    if (e == cudaSuccess) return TGF_OK;
+    *p = nullptr;
+    cudaGetLastError();  // a failed cudaMalloc leaves its error as the thread's last error: clear it
+    if (e == cudaErrorMemoryAllocation)
+        return fail(TGF_ENOMEM, "tgf_create: cudaMalloc of %zu bytes for %s failed: out of device memory", bytes, what);
+    return fail(TGF_ECUDA, "tgf_create: cudaMalloc of %zu bytes for %s: %s", bytes, what, cudaGetErrorString(e));
+}
+
+}  // namespace
+
+struct tgf_ctx {
+    int device = 0, prec = 0, ncfg = 0, reunit_every = 0;
+    unsigned flags = 0;
+    std::vector<tgf_lattice> lat;
+    void* links = nullptr;
+    void* links_tmp = nullptr;
+    void* accum = nullptr;
+    void* scratch = nullptr;
+    double* staging = nullptr;
+    tgf_obs* obs = nullptr;
+    size_t scratch_bytes = 0, staging_bytes = 0, obs_records = 0;
+    ~tgf_ctx() {
+        DeviceGuard g(device);
+        for (void* p : {links, links_tmp, accum, scratch, (void*)staging, (void*)obs})
+            if (p) cudaFree(p);
+    }
+};
+
+namespace {
+
+tgf_status check_ctx(const tgf_ctx* ctx, int cfg, const char* call) {
+    if (!ctx) return fail(TGF_EINVAL, "%s: ctx is NULL", call);
+    if (cfg < -1 || cfg >= ctx->ncfg) return fail(TGF_EINVAL, "%s: configuration %d outside 0..%d", call, cfg, ctx->ncfg - 1);
     return TGF_OK;
+}
+
+tgf_status check_guard(const DeviceGuard& g, int dev) {
+    if (g.err != cudaSuccess) return fail(TGF_ECUDA, "cannot make device %d current: %s", dev, cudaGetErrorString(g.err));
+    return TGF_OK;
+}
+
+// device records of at least n slots, grown on demand
+tgf_status ctx_obs(tgf_ctx* ctx, size_t n) {
+    if (ctx->obs_records >= n) return TGF_OK;
+    if (ctx->obs) cudaFree(ctx->obs);
+    ctx->obs = nullptr;
+    ctx->obs_records = 0;
+    tgf_status s = alloc_dev(reinterpret_cast<void**>(&ctx->obs), n * sizeof(tgf_obs), "the observable records");
+    if (s) return s;
+    ctx->obs_records = n;
+    return TGF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+tgf_status tgf_create(tgf_ctx** out, int device, int prec, int ncfg, const tgf_lattice* lat, int reunit_every,
+                      unsigned flags) {
+    Range range_("tgf_create");
+    tgf_status s;
+    if (!out) return fail(TGF_EINVAL, "tgf_create: out is NULL");
+    *out = nullptr;
+    if ((s = check_prec(prec)) || (s = check_lat(lat, ncfg))) return s;
+    if (reunit_every < 0) return fail(TGF_EINVAL, "tgf_create: reunit_every = %d must be >= 0", reunit_every);
+    if (flags & ~(TGF_CLOVER_TRACELESS | TGF_NO_GRAPH)) return fail(TGF_EINVAL, "tgf_create: unknown flags 0x%x", flags);
+    if (fault_is("alloc"))
+        return fail(TGF_ENOMEM, "tgf_create: device allocation failed (fault injected by TGF_FAULT=alloc)");
+    int ndev = 0;
+    TGF_CUDA(cudaGetDeviceCount(&ndev));
+    if (device < 0 || device >= ndev) return fail(TGF_EINVAL, "tgf_create: device %d outside 0..%d", device, ndev - 1);
+    DeviceGuard g(device);
+    if ((s = check_guard(g, device))) return s;
+    std::unique_ptr<tgf_ctx> c(new tgf_ctx);
+    c->device = device;
+    c->prec = prec;
+    c->ncfg = ncfg;
+    c->reunit_every = reunit_every;
+    c->flags = flags;
+    c->lat.assign(lat, lat + ncfg);
+    const Layout Ly = layout(prec, lat, ncfg);
+    const size_t lb = (size_t)Ly.w_total * real_size(prec), ab = (size_t)Ly.x_total * real_size(prec);
+    c->scratch_bytes = Ly.scratch_bytes(prec);
+    for (int i = 0; i < ncfg; ++i) c->staging_bytes = std::max(c->staging_bytes, (size_t)sites(lat[i]) * 72 * sizeof(double));
+    if ((s = alloc_dev(&c->links, lb, "the links")) || (s = alloc_dev(&c->links_tmp, lb, "the second link buffer")) ||
+        (s = alloc_dev(&c->accum, ab, "the RK3 accumulator")) || (s = alloc_dev(&c->scratch, c->scratch_bytes, "the scratch")) ||
+        (s = alloc_dev(reinterpret_cast<void**>(&c->staging), c->staging_bytes, "the staging buffer")) ||
+        (s = ctx_obs(c.get(), (size_t)ncfg)))
+        return s;
+    TGF_CUDA(cudaMemset(c->links, 0, lb));
+    *out = c.release();
+    return TGF_OK;
+}
+
+void tgf_destroy(tgf_ctx* ctx) { delete ctx; }
+
+tgf_status tgf_set_links(tgf_ctx* ctx, int cfg, const double* host_canon, size_t n_doubles) {
+    Range range_("tgf_set_links");
+    tgf_status s;
+    if ((s = check_ctx(ctx, cfg, "tgf_set_links"))) return s;
+    if (cfg < 0) return fail(TGF_EINVAL, "tgf_set_links: configuration %d outside 0..%d", cfg, ctx->ncfg - 1);
+    if (!host_canon) return fail(TGF_EINVAL, "tgf_set_links: host_canon is NULL");
+    const size_t need = (size_t)sites(ctx->lat[cfg]) * 72;
+    if (n_doubles != need) return fail(TGF_EINVAL, "tgf_set_links: %zu doubles given, configuration %d has %zu", n_doubles, cfg, need);
+    DeviceGuard g(ctx->device);
+    if ((s = check_guard(g, ctx->device))) return s;
+    static const double kNaN = std::numeric_limits<double>::quiet_NaN();
+    TGF_CUDA(cudaMemcpy(ctx->staging, host_canon, need * sizeof(double), cudaMemcpyHostToDevice));
+    if (fault_is("nan")) TGF_CUDA(cudaMemcpy(ctx->staging, &kNaN, sizeof kNaN, cudaMemcpyHostToDevice));
+    const Layout Ly = layout(ctx->prec, ctx->lat.data(), ctx->ncfg);
+    Batch B = make_batch(ctx->lat.data(), Ly, std::vector<int>{cfg}, 32);
+    B.c[0].x_off = 0;
+    launch_pack(ctx->prec, B, ctx->staging, ctx->links, nullptr);
+    if ((s = last_launch("pack"))) return s;
+    TGF_CUDA(cudaStreamSynchronize(nullptr));
+    return TGF_OK;
+}
+
+tgf_status tgf_set_links_device(tgf_ctx* ctx, int cfg, const double* canon_dev, size_t n_doubles, void* stream) {
+    Range range_("tgf_set_links_device");
+    tgf_status s;
+    if ((s = check_ctx(ctx, cfg, "tgf_set_links_device")) || (s = check_ptr(canon_dev, "canon_dev"))) return s;
+    if (cfg < 0) return fail(TGF_EINVAL, "tgf_set_links_device: configuration %d outside 0..%d", cfg, ctx->ncfg - 1);
+    const size_t need = (size_t)sites(ctx->lat[cfg]) * 72;
+    if (n_doubles != need)
+        return fail(TGF_EINVAL, "tgf_set_links_device: %zu doubles given, configuration %d has %zu", n_doubles, cfg, need);
+    DeviceGuard g(ctx->device);
+    if ((s = check_guard(g, ctx->device))) return s;
+    const Layout Ly = layout(ctx->prec, ctx->lat.data(), ctx->ncfg);
+    Batch B = make_batch(ctx->lat.data(), Ly, std::vector<int>{cfg}, 32);
+    B.c[0].x_off = 0;
+    launch_pack(ctx->prec, B, canon_dev, ctx->links, (cudaStream_t)stream);
+    return last_launch("pack");
+}
+
+tgf_status tgf_get_links(tgf_ctx* ctx, int cfg, double* host_canon, size_t n_doubles) {
+    Range range_("tgf_get_links");
+    tgf_status s;
+    if ((s = check_ctx(ctx, cfg, "tgf_get_links"))) return s;
+    if (cfg < 0) return fail(TGF_EINVAL, "tgf_get_links: configuration %d outside 0..%d", cfg, ctx->ncfg - 1);
+    if (!host_canon) return fail(TGF_EINVAL, "tgf_get_links: host_canon is NULL");
+    const size_t need = (size_t)sites(ctx->lat[cfg]) * 72;
+    if (n_doubles != need) return fail(TGF_EINVAL, "tgf_get_links: %zu doubles given, configuration %d has %zu", n_doubles, cfg, need);
+    DeviceGuard g(ctx->device);
+    if ((s = check_guard(g, ctx->device))) return s;
+    const Layout Ly = layout(ctx->prec, ctx->lat.data(), ctx->ncfg);
+    Batch B = make_batch(ctx->lat.data(), Ly, std::vector<int>{cfg}, 32);
+    B.c[0].x_off = 0;
+    launch_unpack(ctx->prec, B, ctx->links, ctx->staging, nullptr);
+    if ((s = last_launch("unpack"))) return s;
+    TGF_CUDA(cudaMemcpy(host_canon, ctx->staging, need * sizeof(double), cudaMemcpyDeviceToHost));
+    return TGF_OK;
+}
+
+tgf_status tgf_ctx_measure(tgf_ctx* ctx, double t, tgf_obs* out, void* stream) {
+    Range range_("tgf_ctx_measure");
+    tgf_status s;
+    if ((s = check_ctx(ctx, -1, "tgf_ctx_measure"))) return s;
+    if (!out) return fail(TGF_EINVAL, "tgf_ctx_measure: out is NULL");
+    DeviceGuard g(ctx->device);
+    if ((s = check_guard(g, ctx->device))) return s;
+    if ((s = tgf_measure(ctx->prec, ctx->lat.data(), ctx->ncfg, ctx->links, static_cast<double*>(ctx->scratch),
+                         ctx->scratch_bytes, ctx->obs, 1, 0, t, (ctx->flags & TGF_CLOVER_TRACELESS) | TGF_SYNC, stream)))
+        return s;
+    TGF_CUDA(cudaMemcpyAsync(out, ctx->obs, (size_t)ctx->ncfg * sizeof(tgf_obs), cudaMemcpyDeviceToHost, (cudaStream_t)stream));
+    TGF_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+    return TGF_OK;
+}
+
+tgf_status tgf_ctx_flow(tgf_ctx* ctx, double eps, const double* t_end, int measure_every, tgf_obs* out, size_t cap,
+                        int* n_written, void* stream) {
+    Range range_("tgf_ctx_flow");
+    tgf_status s;
+    if ((s = check_ctx(ctx, -1, "tgf_ctx_flow"))) return s;
+    if (!out || !t_end || !n_written) return fail(TGF_EINVAL, "tgf_ctx_flow: out, t_end and n_written must not be NULL");
+    if (cap < 1) return fail(TGF_EINVAL, "tgf_ctx_flow: cap = %zu must be >= 1", cap);
+    DeviceGuard g(ctx->device);
+    if ((s = check_guard(g, ctx->device))) return s;
+    for (int c = 0; c < ctx->ncfg; ++c) {
+        int nr = 0;
+        if ((s = tgf_flow_records(eps, t_end[c], measure_every, &nr))) return s;
+        if ((size_t)nr > cap) return fail(TGF_EINVAL, "tgf_ctx_flow: configuration %d needs %d records, cap = %zu", c, nr, cap);
+    }
+    if ((s = ctx_obs(ctx, (size_t)ctx->ncfg * cap))) return s;
+    if ((s = tgf_flow(ctx->prec, ctx->lat.data(), ctx->ncfg, ctx->links, ctx->links_tmp, ctx->accum,
+                      static_cast<double*>(ctx->scratch), ctx->scratch_bytes, eps, t_end, measure_every,
+                      ctx->reunit_every, ctx->flags | TGF_SYNC, ctx->obs, cap, n_written, stream)))
+        return s;
+    TGF_CUDA(cudaMemcpyAsync(out, ctx->obs, (size_t)ctx->ncfg * cap * sizeof(tgf_obs), cudaMemcpyDeviceToHost,
+                             (cudaStream_t)stream));
+    TGF_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+    return TGF_OK;
+}
+
+tgf_status tgf_ctx_save(tgf_ctx* ctx, const char* path, double t, long long step, unsigned long long seed) {
+    tgf_status s;
+    if ((s = check_ctx(ctx, -1, "tgf_ctx_save"))) return s;
+    DeviceGuard g(ctx->device);
+    if ((s = check_guard(g, ctx->device))) return s;
+    return tgf_save(path, ctx->prec, ctx->lat.data(), ctx->ncfg, ctx->links, ctx->staging, ctx->staging_bytes, t, step,
+                    seed, nullptr);
+}
+
+tgf_status tgf_ctx_load(tgf_ctx* ctx, const char* path, double* t, long long* step, unsigned long long* seed) {
+    tgf_status s;
+    if ((s = check_ctx(ctx, -1, "tgf_ctx_load"))) return s;
+    DeviceGuard g(ctx->device);
+    if ((s = check_guard(g, ctx->device))) return s;
+    return tgf_load(path, ctx->prec, ctx->lat.data(), ctx->ncfg, ctx->links, ctx->staging, ctx->staging_bytes, t, step,
+                    seed, nullptr);
 }
 
 }  // extern "C"

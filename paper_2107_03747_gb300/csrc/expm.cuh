@@ -28,6 +28,39 @@ struct series_tol<float> {
     static constexpr float v = 1e-9f;
 };
 
+// Entries of M = f0 + f1 Q + f2 Q^2 (complex f, Hermitian Q and Q^2).  Diagonal: real q = Q_ii,
+// u = (Q^2)_ii.  Off-diagonal pair: m_ij = f1 q + f2 u and m_ji = f1 q* + f2 u* for q = Q_ij,
+// u = (Q^2)_ij.
+template <class T>
+__device__ __forceinline__ void set_diag_entry(cx<T>& m, const cx<T>& f0, const cx<T>& f1, const cx<T>& f2, T q, T u) {
+    m = {f0.re + f1.re * q + f2.re * u, f0.im + f1.im * q + f2.im * u};
+}
+template <class T>
+__device__ __forceinline__ void set_offdiag_pair(cx<T>& mij, cx<T>& mji, const cx<T>& f1, const cx<T>& f2,
+                                                 const cx<T>& q, const cx<T>& u) {
+    mij = {f1.re * q.re - f1.im * q.im + f2.re * u.re - f2.im * u.im,
+           f1.re * q.im + f1.im * q.re + f2.re * u.im + f2.im * u.re};
+    mji = {f1.re * q.re + f1.im * q.im + f2.re * u.re + f2.im * u.im,
+           -f1.re * q.im + f1.im * q.re - f2.re * u.im + f2.im * u.re};
+}
+// FP32 on packed pairs (su3.cuh): with P = f1 q.re + f2 u.re = (A, D) and R = f1 q.im + f2 u.im =
+// (C, B) (f as packed (re, im)), m_ij = (A - B, D + C) = P + (-1, +1) swap(R) and
+// m_ji = (A + B, D - C) = P + (+1, -1) swap(R): 6 packed instructions per pair instead of 16.
+template <>
+__device__ __forceinline__ void set_diag_entry<float>(cx<float>& m, const cx<float>& f0, const cx<float>& f1,
+                                                      const cx<float>& f2, float q, float u) {
+    unpack2(ffma2(as2(f2), pack2(u, u), ffma2(as2(f1), pack2(q, q), as2(f0))), m);
+}
+template <>
+__device__ __forceinline__ void set_offdiag_pair<float>(cx<float>& mij, cx<float>& mji, const cx<float>& f1,
+                                                        const cx<float>& f2, const cx<float>& q, const cx<float>& u) {
+    const f32x2 P = ffma2(as2(f2), re2(u), fmul2(as2(f1), re2(q)));
+    cx<float> R;
+    unpack2(ffma2(as2(f2), im2(u), fmul2(as2(f1), im2(q))), R);
+    unpack2(ffma2(sw2(R), pack2(-1.f, 1.f), P), mij);
+    unpack2(ffma2(sw2(R), pack2(1.f, -1.f), P), mji);
+}
+
 // exp(X) for X given by its 8 parameters (see alg8); with MINUS_ONE, exp(X) - 1 with the unit
 // matrix taken out of the series (f0 - 1 summed from its second term), so that small X keep
 // their full relative precision.
@@ -104,18 +137,13 @@ __device__ __forceinline__ void expm_su3(mat3<T>& m, const alg8<T>& x) {
     cx<T> u12 = {q01.re * q02.re + q01.im * q02.im + (s11 + s22) * q12.re,
                  q01.re * q02.im - q01.im * q02.re + (s11 + s22) * q12.im};
     // M = f0 + f1 Q + f2 Q^2
-    m.e[0][0] = {f0r + f1r * s00 + f2r * d0, f0i + f1i * s00 + f2i * d0};
-    m.e[1][1] = {f0r + f1r * s11 + f2r * d1, f0i + f1i * s11 + f2i * d1};
-    m.e[2][2] = {f0r + f1r * s22 + f2r * d2, f0i + f1i * s22 + f2i * d2};
-#define TGF_OFFDIAG(I, J, QQ, UU)                                                        \
-    m.e[I][J] = {f1r * QQ.re - f1i * QQ.im + f2r * UU.re - f2i * UU.im,                  \
-                 f1r * QQ.im + f1i * QQ.re + f2r * UU.im + f2i * UU.re};                 \
-    m.e[J][I] = {f1r * QQ.re + f1i * QQ.im + f2r * UU.re + f2i * UU.im,                  \
-                 -f1r * QQ.im + f1i * QQ.re - f2r * UU.im + f2i * UU.re};
-    TGF_OFFDIAG(0, 1, q01, u01)
-    TGF_OFFDIAG(0, 2, q02, u02)
-    TGF_OFFDIAG(1, 2, q12, u12)
-#undef TGF_OFFDIAG
+    const cx<T> f0 = {f0r, f0i}, f1 = {f1r, f1i}, f2 = {f2r, f2i};
+    set_diag_entry(m.e[0][0], f0, f1, f2, s00, d0);
+    set_diag_entry(m.e[1][1], f0, f1, f2, s11, d1);
+    set_diag_entry(m.e[2][2], f0, f1, f2, s22, d2);
+    set_offdiag_pair(m.e[0][1], m.e[1][0], f1, f2, q01, u01);
+    set_offdiag_pair(m.e[0][2], m.e[2][0], f1, f2, q02, u02);
+    set_offdiag_pair(m.e[1][2], m.e[2][1], f1, f2, q12, u12);
 #pragma unroll 1
     for (int k = 0; k < s; ++k) {
         mat3<T> t = m;

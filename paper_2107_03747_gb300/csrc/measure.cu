@@ -5,17 +5,31 @@
 // trace.  k_clover_sum adds the halves and accumulates per site
 //   e(n) = sum_{mu<nu} |A_{mu nu}|_F^2            (Tr G^2 = |A|^2 / 64)
 //   q(n) = <A01,A23> - <A02,A13> + <A03,A12>       (Tr G_a G_b = <A_a,A_b> / 64, <X,Y> = Re sum X conj(Y))
-//   p(n) = sum_{mu<nu} Re Tr[Z* P_{mu nu}(n)]
-// in the working precision, then reduces them over the block in FP64 (warp shuffles, fixed
-// order) to one partial per block.  k_reduce sums each configuration's partials in block order
-// and writes {t, E, Q, P, S} with E = sum e/(64 V), Q = sum q/(256 pi^2) (eq. qlatt with
-// Gt_{mu nu} = eps_{mu nu rho sigma} G_{rho sigma}/2), P = sum p/(18 V), S = 18 V - sum p.
+//   s(n) = sum_{mu<nu} (3 - Re Tr[Z* P_{mu nu}(n)])
+// in the working precision (the stage kernel stores each plane's 3 - Re Tr[Z* P], so the small
+// deviations are summed, not six numbers near 3), then reduces them over the block in FP64 (warp
+// shuffles, fixed order) to one partial per block.  k_reduce sums each configuration's partials in
+// block order and writes {t, E, Q, P, S} with E = sum e/(64 V), Q = sum q/(256 pi^2) (eq. qlatt
+// with Gt_{mu nu} = eps_{mu nu rho sigma} G_{rho sigma}/2), S = sum s, P = 1 - S/(18 V).
 // Both orders are fixed: results are bitwise reproducible.
 #include <cuda_runtime.h>
 
 #include "lattice.cuh"
 
 namespace tgf {
+
+// First observable slot (o_off + 1) whose record came out non-finite since the host last read
+// the word; 0 if none.  Read and cleared by nonfinite_read_and_clear().
+__device__ unsigned long long g_nonfinite;
+
+unsigned long long nonfinite_read_and_clear(cudaStream_t st, cudaError_t* err) {
+    unsigned long long v = 0, z = 0;
+    cudaError_t e = cudaMemcpyFromSymbolAsync(&v, g_nonfinite, sizeof v, 0, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyToSymbolAsync(g_nonfinite, &z, sizeof z, 0, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    *err = e;
+    return e == cudaSuccess ? v : 0;
+}
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -122,17 +136,21 @@ k_reduce(const __grid_constant__ BatchT<CAP> B, const double* __restrict__ parti
         const double V = (double)c.V;
         const double pi = 3.14159265358979323846;
         double* o = obs + (size_t)c.o_off * 5;
+        const double E = red[0][0] / (64.0 * V), Q = red[1][0] / (256.0 * pi * pi), S = red[2][0];
         o[0] = c.h;                                   // t
-        o[1] = red[0][0] / (64.0 * V);               // E
-        o[2] = red[1][0] / (256.0 * pi * pi);        // Q
-        o[3] = red[2][0] / (18.0 * V);               // P
-        o[4] = 18.0 * V - red[2][0];                 // S
+        o[1] = E;
+        o[2] = Q;
+        o[3] = 1.0 - S / (18.0 * V);                  // P = (1/(18V)) sum Re Tr[Z* P]
+        o[4] = S;                                     // S = sum (3 - Re Tr[Z* P])
+        // a non-finite record (non-finite links in, or an overflow) is reported to the host
+        if (!isfinite(E) || !isfinite(Q) || !isfinite(S))
+            atomicCAS(&g_nonfinite, 0ull, (unsigned long long)c.o_off + 1ull);
     }
 }
 
 // q(x0, t) (Sec. 4): the charge density summed over the slab x_dir = x of each configuration,
 // one block per (configuration, slab), FP64 sums in a fixed order.  The launch descriptor has
-// L[dir] blocks per configuration; q_out[cfg_index * q_stride + x] with cfg_index = c.rec.
+// L[dir] blocks per configuration; q_out[cfg_index * q_stride + x] with cfg_index = c.o_off.
 template <class T, int CAP>
 __global__ void __launch_bounds__(256)
 k_slice_charge(const __grid_constant__ BatchT<CAP> B, const T* __restrict__ clov, int dir, double* __restrict__ q_out,
@@ -184,7 +202,7 @@ k_slice_charge(const __grid_constant__ BatchT<CAP> B, const T* __restrict__ clov
         }
         if (threadIdx.x == 0) {
             const double pi = 3.14159265358979323846;
-            q_out[(size_t)c.rec * q_stride + x] = red[0] / (256.0 * pi * pi);
+            q_out[(size_t)c.o_off * q_stride + x] = red[0] / (256.0 * pi * pi);
         }
         __syncthreads();
     }

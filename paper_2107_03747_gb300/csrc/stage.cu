@@ -92,7 +92,7 @@ __device__ __forceinline__ void store_ah(T* __restrict__ p, int Vp, int s, const
 // link (n, mu)) and L3 = F' U', L4 = U'^+ B'^+ (from link (n - mu, mu), primed), so
 //   C - C^+ = [D1 - D1^+] + [D2 - D2^+],  D1 = U (F - B) at n,  D2 = (F' - B') U' carried to n.
 // Thread (n, mu) writes D1 - D1^+ to site n and D2 - D2^+ to site n + mu for the planes its warp
-// builds (c_clover_owner), plus Re Tr(U F) (the twisted plaquette at n).
+// builds (c_clover_owner), plus 3 - Re Tr(U F) (the twisted plaquette at n).
 template <int P, int STAGE, int MODE, int SPB, int CAP>
 __global__ void __launch_bounds__(4 * SPB, stage_min_blocks<P>())
 k_stage(const __grid_constant__ BatchT<CAP> B, const typename Store<P>::T* __restrict__ w_in,
@@ -117,7 +117,9 @@ k_stage(const __grid_constant__ BatchT<CAP> B, const typename Store<P>::T* __res
         const CfgDesc& c = B.c[ci];
         const int s = (blk - c.blk0) * SPB + lane;
         const bool valid = s < c.V;
-        const uint64_t xp = valid ? pack_coords(c, s) : 0;
+        int xc[4];
+        site_coords(c, valid ? s : 0, xc);
+        const unsigned eb = edge_bits(c, xc);  // boundary flags (lattice.cuh)
         const int Vp = c.Vp;
         const T* base = w_in + c.w_off;
         auto link = [&](int dir, int site, mat3<T>& u) { S::load(base + (size_t)dir * R * Vp, Vp, site, u); };
@@ -127,8 +129,8 @@ k_stage(const __grid_constant__ BatchT<CAP> B, const typename Store<P>::T* __res
             for (int pr = warp; pr < 6; pr += 4) {
                 if (!valid) break;
                 const int pa = c_pair[pr][0], pb = c_pair[pr][1];
-                link(pb, step_p(s, coord(xp, pa), c.L[pa], c.st[pa]), a);
-                link(pa, step_p(s, coord(xp, pb), c.L[pb], c.st[pb]), b);
+                link(pb, fwd(c, eb, s, pa), a);
+                link(pa, fwd(c, eb, s, pb), b);
                 mul_nd(t, a, b);
 #pragma unroll
                 for (int k = 0; k < 9; ++k) sT[pr][k][lane] = t.e[k / 3][k % 3];
@@ -136,22 +138,21 @@ k_stage(const __grid_constant__ BatchT<CAP> B, const typename Store<P>::T* __res
             __syncthreads();
         }
         auto link_body = [&]() {
-        const int xm = coord(xp, mu), Lm = c.L[mu], Sm = c.st[mu];
-        const int s_mp = step_p(s, xm, Lm, Sm);
+        const int s_mp = fwd(c, eb, s, mu);
+        const bool at_mu0 = (eb >> mu) & 1u;  // x_mu = 0: the twisted plaquettes' corner row
         if (MODE != 2) set_zero(sig);
 #pragma unroll 1
         for (int dn = 1; dn < 4; ++dn) {
             const int nu = (mu + dn) & 3;
             const bool clover = MODE != 0 && c_clover_owner[mu][nu];
             if (MODE == 2 && !clover) continue;
-            const int xn = coord(xp, nu), Ln = c.L[nu], Sn = c.st[nu];
-            const int s_nm = step_m(s, xn, Ln, Sn);
-            const int s_mp_nm = step_p(s_nm, xm, Lm, Sm);
+            const int s_nm = bwd(c, eb, s, nu);
+            const int s_mp_nm = fwd(c, eb, s_nm, mu);  // x_mu(n - nu) = x_mu(n)
             const int k = c.tw[mu * 4 + nu];
             T zr = T(1), zi = T(0);
             if (k != 0) centre<T>(k, zr, zi);
             // forward staple F = Z*_{mu nu}(n) U_nu(n+mu) U_mu(n+nu)^+ U_nu(n)^+ = Z* T_{mu nu} U_nu(n)^+
-            const bool tw_f = k != 0 && xm == 0 && xn == 0;
+            const bool tw_f = k != 0 && at_mu0 && ((eb >> nu) & 1u);
             mat3<T> f;
             if constexpr (SHARE) {
                 // T_{mu nu} = T_{nu mu}^+ from the block's shared T of the plane
@@ -159,8 +160,8 @@ k_stage(const __grid_constant__ BatchT<CAP> B, const typename Store<P>::T* __res
 #pragma unroll
                 for (int kk = 0; kk < 9; ++kk) t.e[kk / 3][kk % 3] = sT[pl_f][kk][lane];
             } else {
-                link(nu, step_p(s, xm, Lm, Sm), a);
-                link(mu, step_p(s, xn, Ln, Sn), b);
+                link(nu, s_mp, a);
+                link(mu, fwd(c, eb, s, nu), b);
                 mul_nd(t, a, b);
             }
             link(nu, s, a);
@@ -187,7 +188,7 @@ k_stage(const __grid_constant__ BatchT<CAP> B, const typename Store<P>::T* __res
             link(nu, s_mp_nm, b);
             mul_nn(t, a, b);
             link(nu, s_nm, a);
-            const bool tw_b = k != 0 && xm == 0 && xn == 1;
+            const bool tw_b = k != 0 && at_mu0 && ((eb >> (8 + nu)) & 1u);
             if (clover || tw_b) {
                 mul_dn(b, t, a);
                 if (tw_b) scale_cx(b, zr, zi);
@@ -199,14 +200,15 @@ k_stage(const __grid_constant__ BatchT<CAP> B, const typename Store<P>::T* __res
                 const int pl = c_plane_of[mu < nu ? mu : nu][mu < nu ? nu : mu];
                 T* cb = clov + c.m_off;
                 link(mu, s, a);  // U = U_mu(n)
-                // Re Tr(U F): the twisted plaquette Z* P_{mu nu}(n)
+                // 3 - Re Tr(U F): the twisted plaquette Z* P_{mu nu}(n) as its deviation from the
+                // unit matrix (exact subtraction for traces in [1.5, 6])
                 T rt = T(0);
 #pragma unroll
                 for (int i = 0; i < 3; ++i)
 #pragma unroll
                     for (int j = 0; j < 3; ++j)
                         rt += a.e[i][j].re * f.e[j][i].re - a.e[i][j].im * f.e[j][i].im;
-                cb[(size_t)(108 + pl) * Vp + s] = rt;
+                cb[(size_t)(108 + pl) * Vp + s] = T(3) - rt;
                 // K = F - B; D1 = U K (site n), D2 = K U (site n + mu).  A plane built through its
                 // second direction (nu < mu) takes K = B - F: the leaves of the plane (mu, nu) are the
                 // Hermitian conjugates of those of (nu, mu), so its C - C^+ changes sign.
@@ -250,10 +252,11 @@ k_stage(const __grid_constant__ BatchT<CAP> B, const typename Store<P>::T* __res
             for (int i = 0; i < 8; ++i) x.v[i] = T(0.75) * h * z.v[i] - x.v[i];
         }
         // W' = W + (exp(X) - 1) W: the update rounds once on top of W instead of through a full
-        // product, which keeps the FP32 forms' drift off SU(3) small between re-projections
+        // product, which keeps the FP32 forms' drift off SU(3) small between re-projections; W
+        // enters the product's accumulators, so the sum costs no separate additions
         expm_su3<T, true>(b, x);
-        mul_nn(t, b, u);
-        add_to(t, u);
+        t = u;
+        mul_nn_acc(t, b, u);
         if (STAGE == 3 && P != P64 && reunit) reunitarize(t);
         S::store(w_out + c.w_off + (size_t)mu * R * Vp, Vp, s, t);
         };

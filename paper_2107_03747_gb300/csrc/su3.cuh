@@ -113,6 +113,25 @@ __device__ __forceinline__ void mul_dn(mat3<T>& c, const mat3<T>& a, const mat3<
         }
 }
 
+// c += a b
+template <class T>
+__device__ __forceinline__ void mul_nn_acc(mat3<T>& c, const mat3<T>& a, const mat3<T>& b) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            T re = c.e[i][j].re, im = c.e[i][j].im;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                re = fma(a.e[i][k].re, b.e[k][j].re, re);
+                re = fma(-a.e[i][k].im, b.e[k][j].im, re);
+                im = fma(a.e[i][k].re, b.e[k][j].im, im);
+                im = fma(a.e[i][k].im, b.e[k][j].re, im);
+            }
+            c.e[i][j] = {re, im};
+        }
+}
+
 // c += a b^+
 template <class T>
 __device__ __forceinline__ void mul_nd_acc(mat3<T>& c, const mat3<T>& a, const mat3<T>& b) {
@@ -247,6 +266,25 @@ __device__ __forceinline__ void mul_dn<float>(mat3<float>& c, const mat3<float>&
             for (int k = 1; k < 3; ++k) {
                 p = ffma2(re2(a.e[k][i]), as2(b.e[k][j]), p);
                 q = ffma2(im2(a.e[k][i]), sw2(b.e[k][j]), q);
+            }
+            unpack2(ffma2(q, s, p), c.e[i][j]);
+        }
+}
+
+// c += a b (the old c enters the accumulator that the combine adds unscaled)
+template <>
+__device__ __forceinline__ void mul_nn_acc<float>(mat3<float>& c, const mat3<float>& a, const mat3<float>& b) {
+    const f32x2 s = pack2(-1.f, 1.f);
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            f32x2 p = ffma2(re2(a.e[i][0]), as2(b.e[0][j]), as2(c.e[i][j]));
+            f32x2 q = fmul2(im2(a.e[i][0]), sw2(b.e[0][j]));
+#pragma unroll
+            for (int k = 1; k < 3; ++k) {
+                p = ffma2(re2(a.e[i][k]), as2(b.e[k][j]), p);
+                q = ffma2(im2(a.e[i][k]), sw2(b.e[k][j]), q);
             }
             unpack2(ffma2(q, s, p), c.e[i][j]);
         }

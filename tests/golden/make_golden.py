@@ -15,8 +15,13 @@ from paper_2107_03747_gb300 import inputs as I  # noqa: E402
 HERE = os.path.dirname(os.path.abspath(__file__))
 
 
-def write_flow(name, L, seed, amp, eps, t_end, note):
-    U = I.random_links(L, seed, amp)
+def write_flow(name, L, seed, amp, eps, t_end, note, batched=False):
+    """Oracle flow of one configuration, every record; `batched` draws the field as a member of
+    the mixed-size ensemble (amplitude from the seed's stream) instead of with amplitude `amp`."""
+    if batched:
+        amp, U = I.batched_member(seed, L)
+    else:
+        U = I.random_links(L, seed, amp)
     t0 = time.time()
     _, rec = O.flow(U, eps, t_end, I.default_twist(1))
     with open(os.path.join(HERE, name), "w") as f:
@@ -28,8 +33,26 @@ def write_flow(name, L, seed, amp, eps, t_end, note):
             f.write(" ".join(repr(float(x)) for x in r) + "\n")
 
 
+FILES = {
+    "flow_l4_seed0.txt": lambda n: write_flow(
+        n, (4, 4, 12, 12), 0, 0.3, 0.01, 0.18,
+        "4x4x12x12 twisted SU(3), links exp(i 0.3 omega T) from seed 0, RK3 eps=0.01 to t=c^2 l^2/8 (c=0.3)"),
+    "flow_l2_seed3.txt": lambda n: write_flow(
+        n, (2, 2, 6, 6), 3, 0.5, 0.02, 0.1,
+        "2x2x6x6 twisted SU(3), links exp(i 0.5 omega T) from seed 3, RK3 eps=0.02 to t=0.1"),
+    # the coupling's own flow time on the L~ = 12 box: sqrt(8t) = c L~ with c = 0.3 (Sec. 3.1), 162 steps
+    "flow_l4_seed0_paper_scale.txt": lambda n: write_flow(
+        n, (4, 4, 12, 12), 0, 0.3, 0.01, 1.62,
+        "4x4x12x12 twisted SU(3), links exp(i 0.3 omega T) from seed 0, RK3 eps=0.01 to sqrt(8t)=0.3*12, t=1.62"),
+    # member 1 (l = 6) of the 256-configuration mixed ensemble, to t = c^2 l^2/8 = 0.405: 40 steps + one of 0.005
+    "flow_l6_batched1.txt": lambda n: write_flow(
+        n, (6, 6, 18, 18), 1, None, 0.01, 0.405,
+        "6x6x18x18 twisted SU(3), mixed-ensemble member seed 1 (amplitude from its stream), RK3 eps=0.01 to "
+        "t=c^2 l^2/8=0.405 (c=0.3)", batched=True),
+}
+
+
 if __name__ == "__main__":
-    write_flow("flow_l4_seed0.txt", (4, 4, 12, 12), 0, 0.3, 0.01, 0.18,
-               "4x4x12x12 twisted SU(3), links exp(i 0.3 omega T) from seed 0, RK3 eps=0.01 to t=c^2 l^2/8 (c=0.3)")
-    write_flow("flow_l2_seed3.txt", (2, 2, 6, 6), 3, 0.5, 0.02, 0.1,
-               "2x2x6x6 twisted SU(3), links exp(i 0.5 omega T) from seed 3, RK3 eps=0.02 to t=0.1")
+    names = sys.argv[1:] or sorted(FILES)
+    for name in names:
+        FILES[name](name)

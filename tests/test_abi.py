@@ -40,6 +40,80 @@ def test_version_and_status_strings(lib):
     assert re.match(r"^\d+\.\d+\.\d+$", lib.version())
     assert lib.status_string(0) == "ok"
     assert lib.status_string(1) == "invalid argument"
+    assert lib.status_string(lib.TGF_ENOMEM) == "out of device memory"
+    assert lib.status_string(lib.TGF_EKERNEL) == "non-finite result"
+
+
+def test_geometry_check_admits_only_the_twisted_box(lib):
+    """Sec. 3.1: the box is l x l x 3l x 3l (SU(N): l x l x Nl x Nl); other extents need TGF_ANY_EXTENTS."""
+    for L in [(4, 4, 12, 11), (4, 5, 12, 12), (4, 4, 8, 8), (12, 12, 4, 4), (3, 3, 5, 7)]:
+        with pytest.raises(lib.TgfError) as e:
+            lib.tgf_links_bytes(lib.TGF_FP32, lib.lattices([L]))
+        assert e.value.status == lib.TGF_EINVAL and "twisted box" in str(e.value)
+        assert lib.tgf_links_bytes(lib.TGF_FP32, lib.lattices([L], any_extents=True)) > 0
+    for l in (2, 3, 4, 16):
+        assert lib.tgf_links_bytes(lib.TGF_FP64, lib.lattices([(l, l, 3 * l, 3 * l)])) > 0
+    # one bad configuration in a batch rejects the batch
+    with pytest.raises(lib.TgfError):
+        lib.tgf_accum_bytes(lib.TGF_FP64, lib.lattices([(4, 4, 12, 12), (4, 4, 12, 10)]))
+    # SU(N): the long extents are N l
+    n = C.c_size_t()
+    assert lib._lib.tgf_sun_links_bytes(2, lib.lattices([(4, 4, 8, 8)]), 1, C.byref(n)) == lib.TGF_OK
+    assert lib._lib.tgf_sun_links_bytes(4, lib.lattices([(2, 2, 8, 8)]), 1, C.byref(n)) == lib.TGF_OK
+    assert lib._lib.tgf_sun_links_bytes(2, lib.lattices([(4, 4, 12, 12)]), 1, C.byref(n)) == lib.TGF_EINVAL
+    # unknown lattice flag bits
+    lat = lib.lattices([(4, 4, 12, 12)])
+    lat[0].flags = 2
+    assert lib._lib.tgf_links_bytes(0, lat, 1, C.byref(n)) == lib.TGF_EINVAL
+
+
+def test_injected_bad_argument_fault(lib, monkeypatch):
+    """TGF_FAULT=badarg: the hot-path argument checks fail with TGF_EINVAL; cleared, the same call passes
+    its checks (here it then fails on the obs capacity, a host check that needs no device)."""
+    lat = lib.lattices([(4, 4, 12, 12)])
+    a = 1 << 20
+    te = (C.c_double * 1)(0.18)
+    nrec = (C.c_int * 1)()
+    sb = lib.tgf_scratch_bytes(0, lat)
+    monkeypatch.setenv("TGF_FAULT", "badarg")
+    s = lib._lib.tgf_flow(0, lat, 1, a, 2 * a, 3 * a, 4 * a, sb, 0.01, te, 1, 0, 0, 5 * a, 100, nrec, None)
+    assert s == lib.TGF_EINVAL and b"TGF_FAULT=badarg" in lib._lib.tgf_last_error()
+    s = lib._lib.tgf_stage(0, lat, 1, a, 2 * a, 3 * a, 1, 0.01, 0, None)
+    assert s == lib.TGF_EINVAL and b"TGF_FAULT=badarg" in lib._lib.tgf_last_error()
+    monkeypatch.delenv("TGF_FAULT")
+    s = lib._lib.tgf_flow(0, lat, 1, a, 2 * a, 3 * a, 4 * a, sb, 0.01, te, 1, 0, 0, 5 * a, 3, nrec, None)
+    assert s == lib.TGF_EINVAL and b"records" in lib._lib.tgf_last_error()
+
+
+def test_injected_allocation_fault(lib, monkeypatch):
+    """TGF_FAULT=alloc: tgf_create reports TGF_ENOMEM and hands back no context (nothing allocated)."""
+    lat = lib.lattices([(4, 4, 12, 12)])
+    h = C.c_void_p(1234)
+    monkeypatch.setenv("TGF_FAULT", "alloc")
+    s = lib._lib.tgf_create(C.byref(h), 0, lib.TGF_FP32, 1, lat, 0, 0)
+    assert s == lib.TGF_ENOMEM and not h.value
+    assert b"TGF_FAULT=alloc" in lib._lib.tgf_last_error()
+    with pytest.raises(lib.TgfError) as e:
+        lib.Context([(4, 4, 12, 12)], "fp32")
+    assert e.value.status == lib.TGF_ENOMEM
+    lib._lib.tgf_destroy(None)  # destroying nothing is allowed
+
+
+@pytest.mark.parametrize("bad", ["null", "reunit", "flags", "extent"])
+def test_create_rejects_bad_arguments(lib, bad):
+    h = C.c_void_p()
+    lat = lib.lattices([(4, 4, 12, 12)])
+    out, reunit, flags = C.byref(h), 0, 0
+    if bad == "null":
+        out = None
+    elif bad == "reunit":
+        reunit = -1
+    elif bad == "flags":
+        flags = 64
+    else:
+        lat = lib.lattices([(4, 4, 12, 13)])
+    assert lib._lib.tgf_create(out, 0, lib.TGF_FP32, 1, lat, reunit, flags) == lib.TGF_EINVAL
+    assert not h.value
 
 
 def test_norm_matches_oracle(lib):
@@ -144,7 +218,7 @@ def test_mc_bad_arguments_are_rejected_before_device_work(lib, bad):
     if bad == "prec":
         prec = lib.TGF_FP32
     elif bad == "odd":
-        lat = lib.lattices([(4, 4, 12, 11)])
+        lat = lib.lattices([(4, 4, 12, 11)], any_extents=True)
     elif bad == "beta":
         beta = 0.0
     elif bad == "count":
@@ -204,7 +278,7 @@ def test_load_rejects_bad_files_before_device_work(lib, tmp_path, bad):
         if bad == "ncfg":
             lat = lib.lattices(Ls * 2)
         elif bad == "extent":
-            lat = lib.lattices([(2, 2, 6, 8)])
+            lat = lib.lattices([(2, 2, 6, 8)], any_extents=True)
         else:
             lat = lib.lattices(Ls, [(2, 0, 0, 0, 0, 0)])
     ptr = 1 << 20  # never dereferenced: every check above fails before the upload
@@ -218,3 +292,23 @@ def test_check_errors_needs_a_self_checking_build(lib):
     assert lib._lib.tgf_check_errors(C.byref(b)) == lib.TGF_EINVAL
     assert b.value == 0
     assert b"TGF_CHECK" in lib._lib.tgf_last_error()
+
+
+def test_multiply_shift_division_reading_is_exact():
+    """The kernels find a site's coordinates as floor(n / d) = floor(16 n m / 2^(32+l)) with
+    l = ceil(log2 d), m = ceil(2^(28+l) / d) (Granlund-Montgomery with the four spare bits of
+    n < 2^28): checked here in exact integer arithmetic for the strides of every box size and for
+    odd divisors, at the multiples of d and their neighbours up to n = 2^28 - 1."""
+    rng = np.random.default_rng(5)
+    divisors = set(range(2, 130)) | {4096, 4095, 2 ** 20 + 1, 3 ** 12, 2 ** 27, 2 ** 28}
+    for l in (2, 4, 6, 8, 12, 16, 24, 48, 72):
+        divisors |= {l, l * l, 3 * l ** 3, l * l * 3 * l}
+    for d in sorted(x for x in divisors if x <= 2 ** 28):
+        sh = (d - 1).bit_length()
+        m = ((1 << (28 + sh)) + d - 1) // d
+        assert m < 2 ** 32
+        k = rng.integers(0, (2 ** 28 - 1) // d + 1, size=400)
+        n = np.concatenate([k * d, k * d - 1, k * d + d - 1, rng.integers(0, 2 ** 28, size=400), [0, 2 ** 28 - 1]])
+        n = [int(v) for v in n if 0 <= v < 2 ** 28]
+        for v in n:
+            assert (((v << 4) * m) >> 32) >> sh == v // d, (d, v)

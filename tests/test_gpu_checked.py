@@ -25,7 +25,7 @@ assert tgf.LIB_PATH.endswith("libtgf_check.so"), tgf.LIB_PATH
 Ls = [(4, 4, 12, 12), (3, 3, 5, 7), (2, 2, 6, 6), (6, 6, 18, 18), (5, 2, 3, 4)]
 fields = [I.random_links(L, 10 + i, 0.5) for i, L in enumerate(Ls)]
 for prec in ("fp64", "fp32", "fp32_r12"):
-    b = tgf.FlowBatch(Ls, prec)
+    b = tgf.FlowBatch(Ls, prec, any_extents=True)
     b.set_links(fields)
     b.flow(0.01, [0.03, 0.02, 0.05, 0.01, 0.025], measure_every=1)
     b.measure()
@@ -39,7 +39,7 @@ tgf.tgf_mc_sweeps(m.prec, m.lat, m.links, 6.0, 1, 2, 5, 0)
 assert tgf.tgf_check_errors() == 0, "mc"
 for N in (2, 3, 4):
     Ls2 = [(2, 2, 2 * N, 2 * N), (3, 2, 4, 5)]
-    s = tgf.SunBatch(N, Ls2)
+    s = tgf.SunBatch(N, Ls2, any_extents=True)
     s.set_links([I.random_links(L, 1, 0.5, N=N) for L in Ls2])
     s.step(0.01)
     s.measure()

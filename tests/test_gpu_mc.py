@@ -21,7 +21,7 @@ TW = I.default_twist(1)
 
 
 def run_gpu(tgf, Ls, fields, beta, n_hybrid, n_or, seed, first):
-    b = tgf.FlowBatch(Ls, "fp64")
+    b = tgf.FlowBatch(Ls, "fp64", any_extents=True)
     b.set_links(fields)
     tgf.tgf_mc_sweeps(b.prec, b.lat, b.links, beta, n_hybrid, n_or, seed, first)
     return b.get_links()

@@ -31,7 +31,7 @@ def close_obs(g, o, rel=1e-12):
 
 
 def batch(tgf, Ls, prec="fp64", twists=None):
-    return tgf.FlowBatch(Ls, prec, twists)
+    return tgf.FlowBatch(Ls, prec, twists, any_extents=True)
 
 
 def load(tgf, Ls, fields, prec="fp64", twists=None):
@@ -249,6 +249,61 @@ def test_flow_fp32_forms_energy_error(tgf, prec):
     assert np.abs(o[:, 2] - ref[:, 2]).max() < 1e-5
 
 
+def test_flow_to_the_paper_scale_matches_stored_oracle_trajectory(tgf):
+    """4x4x12x12 (L~ = 12) flowed to the coupling's own scale sqrt(8t) = 0.3 L~ (Sec. 3.1, eq.
+    lambdat_latt), t = 1.62, 162 steps: FP64 against the stored oracle run at every record to 1e-12,
+    and lambda_TGF of that record against the oracle's."""
+    L = (4, 4, 12, 12)
+    ref = read_golden("flow_l4_seed0_paper_scale.txt")
+    b = load(tgf, [L], [I.random_links(L, 0, 0.3)])
+    obs, n = b.flow(0.01, 1.62)
+    o = obs.cpu().numpy()[0, : n[0]]
+    assert n[0] == len(ref) == 163
+    for g, r in zip(o, ref):
+        close_obs(g, r)
+    lam, kept = tgf.tgf_lambda(0.3, 12, 1.62, [o[-1, 1]], [o[-1, 2]])
+    lo, ko = O.lambda_tgf(0.3, 12, 1.62, [ref[-1, 1]], [ref[-1, 2]])
+    assert kept == ko == 1 and lam == pytest.approx(lo, rel=1e-12)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp32_r12"])
+def test_fp32_forms_to_the_paper_scale_against_the_oracle(tgf, prec):
+    """The FP32 forms over the same 162 steps with the bench's re-projection period (20 steps):
+    |dE/E| <= 1e-6 at every record against the oracle (the configuration has |Q| < 1/2, so it is one
+    lambda_TGF keeps), |dQ| <= 1e-5, P to 1e-6 and S to 1e-5 relative."""
+    L = (4, 4, 12, 12)
+    ref = read_golden("flow_l4_seed0_paper_scale.txt")
+    b = load(tgf, [L], [I.random_links(L, 0, 0.3)], prec)
+    obs, n = b.flow(0.01, 1.62, reunit_every=20)
+    o = obs.cpu().numpy()[0, : n[0]]
+    assert n[0] == len(ref)
+    assert abs(ref[-1, 2]) < 0.5
+    rel = np.abs(o[:, 1] / ref[:, 1] - 1)
+    assert rel.max() <= 1e-6, rel.max()
+    assert np.abs(o[:, 2] - ref[:, 2]).max() <= 1e-5
+    assert np.abs(o[:, 3] / ref[:, 3] - 1).max() <= 1e-6
+    assert np.abs(o[:, 4] / ref[:, 4] - 1).max() <= 1e-5
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp32_r12"])
+def test_fp32_forms_on_the_l6_ensemble_member_against_the_oracle(tgf, prec):
+    """6x6x18x18 member of the mixed ensemble (seed 1) to t = c^2 l^2/8 = 0.405, 40 steps and one of
+    0.005: the FP32 forms against the stored oracle trajectory at every record, |dE/E| <= 1e-6."""
+    L = (6, 6, 18, 18)
+    ref = read_golden("flow_l6_batched1.txt")
+    _, U = I.batched_member(1, L)
+    b = load(tgf, [L], [U], prec)
+    obs, n = b.flow(0.01, 0.405, reunit_every=20)
+    o = obs.cpu().numpy()[0, : n[0]]
+    assert n[0] == len(ref) == 42
+    assert o[:, 0] == pytest.approx(ref[:, 0], abs=1e-12)
+    rel = np.abs(o[:, 1] / ref[:, 1] - 1)
+    assert rel.max() <= 1e-6, rel.max()
+    assert np.abs(o[:, 2] - ref[:, 2]).max() <= 1e-5
+    assert np.abs(o[:, 3] / ref[:, 3] - 1).max() <= 1e-6
+    assert np.abs(o[:, 4] / ref[:, 4] - 1).max() <= 1e-5
+
+
 def test_flow_is_reproducible_bitwise(tgf):
     L = (4, 4, 12, 12)
     U = I.random_links(L, 9, 0.5)
@@ -371,7 +426,7 @@ def test_upload_download_through_host_buffers(tgf, prec):
     Ls = [(4, 4, 12, 12), (3, 3, 5, 7), (2, 2, 6, 6)]
     fields = [I.random_links(L, 90 + i, 0.5) for i, L in enumerate(Ls)]
     host = torch.from_numpy(np.concatenate([f.view(np.float64).reshape(-1) for f in fields])).pin_memory()
-    b = tgf.FlowBatch(Ls, prec)
+    b = tgf.FlowBatch(Ls, prec, any_extents=True)
     staging = torch.empty(max(L[0] * L[1] * L[2] * L[3] for L in Ls) * 72, dtype=torch.float64, device="cuda")
     tgf.tgf_upload(b.prec, b.lat, host, staging, b.links)
     ref = b.get_links()

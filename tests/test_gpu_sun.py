@@ -29,7 +29,7 @@ def fields_for(N):
 @pytest.mark.parametrize("N", [2, 3, 4])
 def test_sun_pack_roundtrip_and_measure(tgf, N):
     Ls, fs = fields_for(N)
-    b = tgf.SunBatch(N, Ls)
+    b = tgf.SunBatch(N, Ls, any_extents=True)
     b.set_links(fs)
     for f, g in zip(fs, b.get_links()):
         assert np.array_equal(f, g)
@@ -42,7 +42,7 @@ def test_sun_pack_roundtrip_and_measure(tgf, N):
 @pytest.mark.parametrize("N", [2, 3, 4])
 def test_sun_rk3_step_matches_oracle(tgf, N):
     Ls, fs = fields_for(N)
-    b = tgf.SunBatch(N, Ls)
+    b = tgf.SunBatch(N, Ls, any_extents=True)
     b.set_links(fs)
     b.step(0.02)
     b.step(0.02)

@@ -24,7 +24,7 @@ def test_noalloc_matches_caller_scratch_twice_in_a_row(tgf, prec):
     fields = [[I.random_links(L, 60 + i + 10 * r, 0.5) for i, L in enumerate(Ls)] for r in range(2)]
     rel = 1e-12 if prec == "fp64" else 1e-6
     for r in range(2):
-        b = tgf.FlowBatch(Ls, prec)
+        b = tgf.FlowBatch(Ls, prec, any_extents=True)
         b.set_links(fields[r])
         ref = b.measure(t=0.125)  # tgf_measure, scratch from the caller
         obs = torch.full((len(Ls) * 5,), float("nan"), dtype=torch.float64, device="cuda")
