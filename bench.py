@@ -376,6 +376,12 @@ def roofline_of(tgf, prec_name, V, stage_ms, meas_ms, workload, peaks, hbm_peak)
             "measure_ms": meas_ms, "measure_tflops": MEAS_FLOP * V / (meas_ms * 1e-3) / 1e12}
 
 
+def tune_setting(flags):
+    from paper_2107_03747_gb300 import tune
+
+    return tune.flags_setting(flags)
+
+
 def hbm_peak_gbs():
     try:
         return float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"])
@@ -441,11 +447,21 @@ def profile_stages(args):
     b = tgf.FlowBatch(Ls, args.profile_stages)
     tgf.tgf_pack(b.prec, b.lat, canon, b.links)
     del canon
-    for _ in range(args.steps):
-        for s in (1, 2, 3):
-            tgf.tgf_stage(b.prec, b.lat, b.links, b.links_tmp, b.accum, s, EPS, 0)
+    if args.tile is None:
+        for _ in range(args.steps):
+            for s in (1, 2, 3):
+                tgf.tgf_stage(b.prec, b.lat, b.links, b.links_tmp, b.accum, s, EPS, 0)
+    else:
+        # the flow's own launches with the given launch tile: one measured step first (stage 1 with
+        # the clover halves), then args.steps unmeasured steps; direct launches, no graph
+        from paper_2107_03747_gb300 import tune
+
+        obs = torch.zeros(len(Ls) * 4 * 5, dtype=torch.float64, device="cuda")
+        tgf.tgf_flow(b.prec, b.lat, b.links, b.links_tmp, b.accum, b.scratch, EPS, [EPS * (args.steps + 1)] * len(Ls),
+                     obs, 4, 10 ** 6, 0, tune.tune_flags(0, False, args.tile) | tgf.TGF_NO_GRAPH)
     torch.cuda.synchronize()
-    print(json.dumps({"profile_stages": args.profile_stages, "workload": args.workload, "launches": 3 * args.steps}))
+    print(json.dumps({"profile_stages": args.profile_stages, "workload": args.workload, "tile": args.tile,
+                      "launches": 3 * args.steps}))
     return 0
 
 
@@ -643,8 +659,7 @@ def run_tgf(args):
                        "l2": ("inputs larger than L2" if link_bytes > L2_BYTES else "inputs smaller than L2") +
                              f" ({link_bytes / 1e6:.0f} MB links, {canon_bytes / 1e6:.0f} MB canonical)",
                        "parallelism": f"replicas x{ws}", "graph": True,
-                       "launch_tuning": {"flags": flags, "grid_k": (flags >> 8) & 0xF,
-                                         "size_order": bool(flags & (1 << 12)), "tuned": bool(args.tune)}},
+                       "launch_tuning": dict(flags=flags, tuned=bool(args.tune), **tune_setting(flags))},
             "e2e": {"value": e2e_value, "unit": "site-steps/s", "h2d_bytes_per_step": canon_bytes,
                     "d2h_bytes_per_step": obs_host.numel() * 8, "ms_per_step": ms_e2e},
             "gpu_launches": launches_per_flow(members) * args.steps,
@@ -721,6 +736,7 @@ def run_batched(tgf, dev, stream, args):
     work = site_steps(members)
     acc = accuracy_vs(o, o64, nrec, lam_of(tgf, o, nrec, Ls), lam_of(tgf, o64, nrec64, Ls))
     return {"workload": WORKLOADS["mixed256"]["desc"], "precision": "fp32", "launch_flags": flags,
+            "launch_tuning": tune_setting(flags),
             "value": work / (ms * 1e-3), "ms_per_step": ms, "fp64_loop_value": work / dt, "fp64_loop_seconds": dt,
             "speedup_vs_fp64_loop": dt / (ms * 1e-3),
             "fp64_loop": "each configuration flowed alone in FP64, kernels launched directly (no graph), host clock",
@@ -746,6 +762,8 @@ def main():
                     help="oracle units in the cpu_baseline pool (default: one per host core, memory permitting)")
     ap.add_argument("--profile-stages", default=None, choices=list(PREC_NAMES),
                     help="only run the stage kernels of the workload in this precision (ncu traffic captures)")
+    ap.add_argument("--tile", type=int, default=None, choices=[0, 1, 2, 3],
+                    help="with --profile-stages: run the flow's launches with this launch tile")
     args = ap.parse_args()
     if args.cpu_units <= 0:
         args.cpu_units = os.cpu_count() or 1

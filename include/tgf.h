@@ -107,6 +107,13 @@ typedef enum {
  * TGF_TUNE_SIZE_ORDER orders the configurations of each launch by size, largest first. */
 #define TGF_TUNE_GRID(k) (((unsigned)(k) & 0xFu) << 8)
 #define TGF_TUNE_SIZE_ORDER (1u << 12)
+/* TGF_TUNE_TILE(t): launch tile of the FP32 forms' stage kernels -- 0: 32 sites per block, one
+ * warp per direction, up to 128 registers; 1: 64 sites per block (two warps per direction); 2: 32
+ * sites per block with up to 168 registers (3 resident blocks per SM); 3: as 0, with the
+ * forward-staple corners U_b(n+a) U_a(n+b)^+ of the unmeasured stages formed once per pair of
+ * direction warps and passed through shared memory (results equal up to rounding).  Tiles 0-2
+ * give bitwise the same flow.  Ignored in FP64. */
+#define TGF_TUNE_TILE(t) (((unsigned)(t) & 0x3u) << 13)
 
 typedef struct {
     int L[4];        /* extents, x0 fastest                                          */
@@ -320,7 +327,8 @@ tgf_status tgf_mc_sweeps(int prec, const tgf_lattice *lat, int ncfg, void *links
  * clover access against the plane length in the kernels; a violation is recorded in a device
  * word of the kernel's source file and the access is redirected to site 0 (no fault).  This call
  * synchronises the device and returns the words as bits (1 stage kernels, 2 measurement, 4
- * layout, 8 Monte Carlo, 16 SU(N)) and clears them; 0 means no violation since the last call.
+ * layout, 8 Monte Carlo, 16 SU(N), 32 stage kernels of the other launch tiles) and clears them;
+ * 0 means no violation since the last call.
  * In a normal build it returns TGF_EINVAL.  The paper has no counterpart: it replaces a memory
  * checker where none can run. */
 tgf_status tgf_check_errors(unsigned int *bits);

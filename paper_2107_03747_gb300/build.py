@@ -16,7 +16,7 @@ CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libtgf.so")
 
-SOURCES = ["stage.cu", "measure.cu", "pack.cu", "api.cu", "peak.cu", "measure_static.cu", "mc.cu", "sun.cu", "coupling.cpp"]
+SOURCES = ["stage.cu", "stage_tiles.cu", "measure.cu", "pack.cu", "api.cu", "peak.cu", "measure_static.cu", "mc.cu", "sun.cu", "coupling.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -482,10 +482,10 @@ tgf_status tgf_check_errors(unsigned* bits) {
     if (!bits) return fail(TGF_EINVAL, "bits is NULL");
 #ifdef TGF_CHECK
     TGF_CUDA(cudaDeviceSynchronize());
-    const unsigned w[5] = {check_word_stage(), check_word_measure(), check_word_pack(), check_word_mc(),
-                           check_word_sun()};
+    const unsigned w[6] = {check_word_stage(), check_word_measure(), check_word_pack(), check_word_mc(),
+                           check_word_sun(), check_word_stage_tiles()};
     unsigned b = 0;
-    for (int i = 0; i < 5; ++i)
+    for (int i = 0; i < 6; ++i)
         if (w[i]) b |= 1u << i;
     *bits = b;
     return TGF_OK;
@@ -861,9 +861,13 @@ static tgf_status enqueue_flow(int prec, const tgf_lattice* lat, int ncfg, const
         int dev = 0, sms = 0;
         TGF_CUDA(cudaGetDevice(&dev));
         TGF_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-        grid = k * sms * (prec == TGF_FP64 ? 2 : 4);
+        const unsigned t = (flags >> 13) & 0x3u;  // resident blocks per SM of the tile
+        grid = k * sms * (prec == TGF_FP64 ? 2 : t == 1 ? 2 : t == 2 ? 3 : 4);
     }
     const bool by_size = (flags & TGF_TUNE_SIZE_ORDER) != 0;
+    // launch tile of the FP32 forms' stage kernels (FP64 has one tile)
+    const int tile = prec == TGF_FP64 ? 0 : (int)((flags >> 13) & 0x3u);
+    if (tile >= kTiles) return fail(TGF_EINVAL, "tgf_flow: launch tile %d outside 0..%d", tile, kTiles - 1);
     void* cur = w;
     void* alt = w_tmp;
     SideBranch side;
@@ -899,14 +903,14 @@ static tgf_status enqueue_flow(int prec, const tgf_lattice* lat, int ncfg, const
         const int mode1 = mw.empty() ? 0 : 1;
         if (by_size)
             std::stable_sort(act.begin(), act.end(), [&](int a, int b) { return sites(lat[a]) > sites(lat[b]); });
-        Batch B = make_batch(lat, Ly, act, 32);
+        Batch B = make_batch(lat, Ly, act, tile_sites(tile));
         for (int k = 0; k < B.ncfg; ++k) {
             const int c = act[k];
             B.c[k].h = (i < n[c]) ? eps : rest[c];
         }
         const int ru = (prec != TGF_FP64 && reunit_every > 0 && (i + 1) % reunit_every == 0) ? 1 : 0;
         if (mode1 && (s = join())) return s;  // stage 1 is about to rewrite the halves
-        launch_stage(prec, 1, mode1, 0, B, cur, alt, accum, clover_base(scratch, Ly), st, grid);
+        launch_stage(prec, 1, mode1, 0, B, cur, alt, accum, clover_base(scratch, Ly), st, grid, tile);
         if ((s = last_launch("stage 1"))) return s;
         if (mode1) {
             TGF_CUDA(cudaEventRecord(sb->fork, st));
@@ -915,9 +919,9 @@ static tgf_status enqueue_flow(int prec, const tgf_lattice* lat, int ncfg, const
             TGF_CUDA(cudaEventRecord(sb->join, sb->s));
             pending = true;
         }
-        launch_stage(prec, 2, 0, 0, B, alt, cur, accum, nullptr, st, grid);
+        launch_stage(prec, 2, 0, 0, B, alt, cur, accum, nullptr, st, grid, tile);
         if ((s = last_launch("stage 2"))) return s;
-        launch_stage(prec, 3, 0, ru, B, cur, alt, accum, nullptr, st, grid);
+        launch_stage(prec, 3, 0, ru, B, cur, alt, accum, nullptr, st, grid, tile);
         if ((s = last_launch("stage 3"))) return s;
         std::swap(cur, alt);
         std::vector<int> fw, fr;

@@ -156,6 +156,7 @@ __device__ __forceinline__ int checked_site(int s, int) { return s; }
 
 // per translation unit check words of a self-checking build
 unsigned check_word_stage();
+unsigned check_word_stage_tiles();
 unsigned check_word_measure();
 unsigned check_word_pack();
 unsigned check_word_mc();
@@ -283,6 +284,15 @@ struct Store<P32R12> {
         u.e[1][1] = {b.x, b.y}; u.e[1][2] = {b.z, b.w};
         rebuild_row2(u);
     }
+    // rows 0 and 1 only (row 2 of u left as it was)
+    static __device__ __forceinline__ void load_top(const float* __restrict__ base, int Vp, int s, mat3<float>& u) {
+        s = checked_site(s, Vp);
+        float a[8];
+        ld8_nc(base + (size_t)s * 8, a);
+        const float4 b = __ldg(reinterpret_cast<const float4*>(base + (size_t)8 * Vp) + s);
+        u.e[0][0] = {a[0], a[1]}; u.e[0][1] = {a[2], a[3]}; u.e[0][2] = {a[4], a[5]}; u.e[1][0] = {a[6], a[7]};
+        u.e[1][1] = {b.x, b.y}; u.e[1][2] = {b.z, b.w};
+    }
     static __device__ __forceinline__ void store(float* __restrict__ base, int Vp, int s, const mat3<float>& u) {
         s = checked_site(s, Vp);
         const float a[8] = {u.e[0][0].re, u.e[0][0].im, u.e[0][1].re, u.e[0][1].im,
@@ -340,8 +350,14 @@ int set_error(int st, const char* fmt, ...);
 
 // mode: 0 = RK3 stage only; 1 = stage and clover halves of the input field; 2 = halves only
 // grid > 0 launches that many blocks (a grid-stride loop covers B.nblk tiles); 0 = one block per tile
+// tile: the launch tile of the FP32 forms (stage_kernel.cuh; 0 for FP64 and mode 2); the batch must
+// have been built with tile_sites(tile) sites per block
 void launch_stage(int prec, int stage, int mode, int reunit, const Batch& B, const void* w_in, void* w_out,
-                  void* acc, void* clov, cudaStream_t st, int grid = 0);
+                  void* acc, void* clov, cudaStream_t st, int grid = 0, int tile = 0);
+void launch_stage_tile(int tile, int prec, int stage, int mode, int reunit, const Batch& B, const void* w_in,
+                       void* w_out, void* acc, void* clov, cudaStream_t st, int grid);
+constexpr int kTiles = 4;
+inline int tile_sites(int tile) { return tile == 1 ? 64 : 32; }
 void launch_clover_sum(int prec, unsigned flags, const Batch& B, const void* clov, double* partial,
                        cudaStream_t st);
 void launch_reduce(const Batch& B, const double* partial, double* obs, cudaStream_t st);

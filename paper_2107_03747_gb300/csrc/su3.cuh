@@ -113,23 +113,13 @@ __device__ __forceinline__ void mul_dn(mat3<T>& c, const mat3<T>& a, const mat3<
         }
 }
 
-// c += a b
+// c = a b + w with the product formed first and w added once: when a b is small next to w (the
+// flow's update W + (exp(X) - 1) W) every rounding of the product is relative to the small term,
+// and the sum rounds only once on top of w
 template <class T>
-__device__ __forceinline__ void mul_nn_acc(mat3<T>& c, const mat3<T>& a, const mat3<T>& b) {
-#pragma unroll
-    for (int i = 0; i < 3; ++i)
-#pragma unroll
-        for (int j = 0; j < 3; ++j) {
-            T re = c.e[i][j].re, im = c.e[i][j].im;
-#pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                re = fma(a.e[i][k].re, b.e[k][j].re, re);
-                re = fma(-a.e[i][k].im, b.e[k][j].im, re);
-                im = fma(a.e[i][k].re, b.e[k][j].im, im);
-                im = fma(a.e[i][k].im, b.e[k][j].re, im);
-            }
-            c.e[i][j] = {re, im};
-        }
+__device__ __forceinline__ void mul_nn_plus(mat3<T>& c, const mat3<T>& a, const mat3<T>& b, const mat3<T>& w) {
+    mul_nn(c, a, b);
+    add_to(c, w);
 }
 
 // c += a b^+
@@ -165,6 +155,77 @@ __device__ __forceinline__ void mul_dn_acc(mat3<T>& c, const mat3<T>& a, const m
                 re = fma(a.e[k][i].im, b.e[k][j].im, re);
                 im = fma(a.e[k][i].re, b.e[k][j].im, im);
                 im = fma(-a.e[k][i].im, b.e[k][j].re, im);
+            }
+            c.e[i][j] = {re, im};
+        }
+}
+
+// Rows 0 and 1 of c = a b^+ and of c = a b (row 2 of c untouched): with a, b in SU(3) the product
+// is in SU(3) and its row 2 follows as conj(row0 x row1) (rebuild_row2), so a factor stored as
+// two rows needs no rebuilt third row of its own.
+template <class T>
+__device__ __forceinline__ void mul_nd_top(mat3<T>& c, const mat3<T>& a, const mat3<T>& b) {
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            T re = T(0), im = T(0);
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                re = fma(a.e[i][k].re, b.e[j][k].re, re);
+                re = fma(a.e[i][k].im, b.e[j][k].im, re);
+                im = fma(a.e[i][k].im, b.e[j][k].re, im);
+                im = fma(-a.e[i][k].re, b.e[j][k].im, im);
+            }
+            c.e[i][j] = {re, im};
+        }
+}
+template <class T>
+__device__ __forceinline__ void mul_nn_top(mat3<T>& c, const mat3<T>& a, const mat3<T>& b) {
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            T re = T(0), im = T(0);
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                re = fma(a.e[i][k].re, b.e[k][j].re, re);
+                re = fma(-a.e[i][k].im, b.e[k][j].im, re);
+                im = fma(a.e[i][k].re, b.e[k][j].im, im);
+                im = fma(a.e[i][k].im, b.e[k][j].re, im);
+            }
+            c.e[i][j] = {re, im};
+        }
+}
+
+// rows 0 and 1 of c = a b + w (the product formed first, as mul_nn_plus)
+template <class T>
+__device__ __forceinline__ void mul_nn_plus_top(mat3<T>& c, const mat3<T>& a, const mat3<T>& b, const mat3<T>& w) {
+    mul_nn_top(c, a, b);
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            c.e[i][j].re += w.e[i][j].re;
+            c.e[i][j].im += w.e[i][j].im;
+        }
+}
+
+// c += a^+ b^+
+template <class T>
+__device__ __forceinline__ void mul_dd_acc(mat3<T>& c, const mat3<T>& a, const mat3<T>& b) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            // sum_k conj(a_ki) conj(b_jk)
+            T re = c.e[i][j].re, im = c.e[i][j].im;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                re = fma(a.e[k][i].re, b.e[j][k].re, re);
+                re = fma(-a.e[k][i].im, b.e[j][k].im, re);
+                im = fma(-a.e[k][i].re, b.e[j][k].im, im);
+                im = fma(-a.e[k][i].im, b.e[j][k].re, im);
             }
             c.e[i][j] = {re, im};
         }
@@ -271,22 +332,28 @@ __device__ __forceinline__ void mul_dn<float>(mat3<float>& c, const mat3<float>&
         }
 }
 
-// c += a b (the old c enters the accumulator that the combine adds unscaled)
+// c = a b + w: the packed product, then one packed add of w per entry
+__device__ __forceinline__ f32x2 fadd2(f32x2 a, f32x2 b) {
+    f32x2 d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
 template <>
-__device__ __forceinline__ void mul_nn_acc<float>(mat3<float>& c, const mat3<float>& a, const mat3<float>& b) {
+__device__ __forceinline__ void mul_nn_plus<float>(mat3<float>& c, const mat3<float>& a, const mat3<float>& b,
+                                                   const mat3<float>& w) {
     const f32x2 s = pack2(-1.f, 1.f);
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
         for (int j = 0; j < 3; ++j) {
-            f32x2 p = ffma2(re2(a.e[i][0]), as2(b.e[0][j]), as2(c.e[i][j]));
+            f32x2 p = fmul2(re2(a.e[i][0]), as2(b.e[0][j]));
             f32x2 q = fmul2(im2(a.e[i][0]), sw2(b.e[0][j]));
 #pragma unroll
             for (int k = 1; k < 3; ++k) {
                 p = ffma2(re2(a.e[i][k]), as2(b.e[k][j]), p);
                 q = ffma2(im2(a.e[i][k]), sw2(b.e[k][j]), q);
             }
-            unpack2(ffma2(q, s, p), c.e[i][j]);
+            unpack2(fadd2(ffma2(q, s, p), as2(w.e[i][j])), c.e[i][j]);
         }
 }
 
@@ -323,6 +390,62 @@ __device__ __forceinline__ void mul_dn_acc<float>(mat3<float>& c, const mat3<flo
             for (int k = 1; k < 3; ++k) {
                 p = ffma2(re2(a.e[k][i]), as2(b.e[k][j]), p);
                 q = ffma2(im2(a.e[k][i]), sw2(b.e[k][j]), q);
+            }
+            unpack2(ffma2(q, s, p), c.e[i][j]);
+        }
+}
+
+// c += a^+ b^+ = conj(a^T b^T): with p = sum re(a_ki) (b_jk) and q = sum im(a_ki) swap(b_jk) the
+// entry is (p.x - q.x, -p.y - q.y), two sign-applying FMAs onto c
+template <>
+__device__ __forceinline__ void mul_dd_acc<float>(mat3<float>& c, const mat3<float>& a, const mat3<float>& b) {
+    const f32x2 sp = pack2(1.f, -1.f), sq = pack2(-1.f, -1.f);
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            f32x2 p = fmul2(re2(a.e[0][i]), as2(b.e[j][0]));
+            f32x2 q = fmul2(im2(a.e[0][i]), sw2(b.e[j][0]));
+#pragma unroll
+            for (int k = 1; k < 3; ++k) {
+                p = ffma2(re2(a.e[k][i]), as2(b.e[j][k]), p);
+                q = ffma2(im2(a.e[k][i]), sw2(b.e[j][k]), q);
+            }
+            unpack2(ffma2(q, sq, ffma2(p, sp, as2(c.e[i][j]))), c.e[i][j]);
+        }
+}
+
+// rows 0 and 1 of c = a b^+ and c = a b on packed pairs
+template <>
+__device__ __forceinline__ void mul_nd_top<float>(mat3<float>& c, const mat3<float>& a, const mat3<float>& b) {
+    const f32x2 s = pack2(1.f, -1.f);
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            f32x2 p = fmul2(re2(a.e[i][0]), as2(b.e[j][0]));
+            f32x2 q = fmul2(im2(a.e[i][0]), sw2(b.e[j][0]));
+#pragma unroll
+            for (int k = 1; k < 3; ++k) {
+                p = ffma2(re2(a.e[i][k]), as2(b.e[j][k]), p);
+                q = ffma2(im2(a.e[i][k]), sw2(b.e[j][k]), q);
+            }
+            unpack2(ffma2(p, s, q), c.e[i][j]);
+        }
+}
+template <>
+__device__ __forceinline__ void mul_nn_top<float>(mat3<float>& c, const mat3<float>& a, const mat3<float>& b) {
+    const f32x2 s = pack2(-1.f, 1.f);
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            f32x2 p = fmul2(re2(a.e[i][0]), as2(b.e[0][j]));
+            f32x2 q = fmul2(im2(a.e[i][0]), sw2(b.e[0][j]));
+#pragma unroll
+            for (int k = 1; k < 3; ++k) {
+                p = ffma2(re2(a.e[i][k]), as2(b.e[k][j]), p);
+                q = ffma2(im2(a.e[i][k]), sw2(b.e[k][j]), q);
             }
             unpack2(ffma2(q, s, p), c.e[i][j]);
         }

@@ -1,9 +1,10 @@
 """Launch tuner of tgf_flow: times the launch settings on the actual workload and caches the winner.
 
-The settings (tgf.h: TGF_TUNE_GRID(k), TGF_TUNE_SIZE_ORDER) change how the stage kernels are
-scheduled, never what they compute: a persistent grid of k x SMs x resident blocks that loops
-over the 32-site tiles (k = 0: one block per tile), and the order of the configurations inside
-each launch (as given, or largest first).  For a workload -- precision, the multiset of
+The settings (tgf.h: TGF_TUNE_GRID(k), TGF_TUNE_SIZE_ORDER, TGF_TUNE_TILE(t)) change how the
+stage kernels are scheduled, never what they compute: the launch tile of the FP32 forms (32 or 64
+sites per block, and the register cap that sets how many blocks share an SM), a persistent grid
+of k x SMs x resident blocks that loops over the tiles (k = 0: one block per tile), and the order
+of the configurations inside each launch (as given, or largest first).  For a workload -- precision, the multiset of
 extents, measurement interval -- the tuner flows the batch for a few steps under every
 candidate (each captured as its own CUDA graph), times the best of `reps` replays with CUDA
 events, and stores the fastest flags in a JSON cache (path from TGF_TUNE_CACHE, else
@@ -17,15 +18,30 @@ from collections import Counter
 
 GRIDS = (0, 1, 2, 4)
 ORDERS = (False, True)
+# launch tiles of the FP32 forms' stage kernels (tgf.h TGF_TUNE_TILE): 32 sites per block with up
+# to 128 registers, 64 sites per block (two warps per direction), 32 sites with up to 168 registers,
+# 32 sites with the forward-staple corners shared in pairs of direction warps
+TILES = (0, 1, 2, 3)
 TGF_TUNE_SIZE_ORDER = 1 << 12
+TGF_FP64 = 0
 
 
-def tune_flags(grid: int, by_size: bool) -> int:
-    return ((grid & 0xF) << 8) | (TGF_TUNE_SIZE_ORDER if by_size else 0)
+def tune_flags(grid: int, by_size: bool, tile: int = 0) -> int:
+    return ((grid & 0xF) << 8) | (TGF_TUNE_SIZE_ORDER if by_size else 0) | ((tile & 0x3) << 13)
 
 
-def candidates():
-    return [tune_flags(g, o) for g in GRIDS for o in ORDERS]
+def flags_setting(flags: int) -> dict:
+    """The launch setting a flags word selects (reported next to bench numbers)."""
+    return {"grid_k": (flags >> 8) & 0xF, "size_order": bool(flags & TGF_TUNE_SIZE_ORDER),
+            "tile": (flags >> 13) & 0x3, "sites_per_block": 64 if (flags >> 13) & 0x3 == 1 else 32,
+            "resident_blocks_per_sm": {0: 4, 1: 2, 2: 3, 3: 4}[(flags >> 13) & 0x3],
+            "shared_corners": (flags >> 13) & 0x3 == 3}
+
+
+def candidates(prec: int | None = None):
+    """Every setting of the search space; FP64 has the default tile only."""
+    tiles = (0,) if prec == TGF_FP64 else TILES
+    return [tune_flags(g, o, t) for t in tiles for g in GRIDS for o in ORDERS]
 
 
 def workload_key(prec: int, Ls, measure_every: int) -> str:
@@ -76,7 +92,7 @@ def tune(batch, eps: float = 0.01, steps: int = 4, measure_every: int = 1, reps:
             return int(hit["flags"])
     if timer is None:
         timer = _gpu_timer(batch, eps, steps, measure_every, reps)
-    times = {f: float(timer(f)) for f in candidates()}
+    times = {f: float(timer(f)) for f in candidates(batch.prec)}
     best = choose(times)
     store(key, {"flags": best, "ms": {str(f): t for f, t in times.items()}, "steps": steps}, path)
     return best

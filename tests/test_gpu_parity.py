@@ -505,19 +505,56 @@ def test_launch_tuning_settings_give_identical_flows(tgf, prec, tmp_path):
     fields = [I.random_links(L, 70 + i, 0.5) for i, L in enumerate(Ls)]
     t_end = [0.05, 0.03, 0.04, 0.05]
     ref = None
-    for f in tune.candidates():
+    for f in tune.candidates(tgf.PRECISIONS[prec]):
         b = load(tgf, Ls, fields, prec)
         obs, nrec = b.flow(0.01, t_end, flags=f)
         got = (b.get_links(), obs.cpu().numpy(), list(nrec))
         if ref is None:
             ref = got
             continue
-        assert all(np.array_equal(x, y) for x, y in zip(ref[0], got[0]))
-        assert np.array_equal(ref[1], got[1]) and ref[2] == got[2]
+        assert ref[2] == got[2]
+        if tune.flags_setting(f)["shared_corners"]:
+            # tile 3 forms half the forward staples as (Z T_ba)^+ U^+: equal up to FP32 rounding
+            assert all(np.abs(x - y).max() < 2e-6 for x, y in zip(ref[0], got[0]))
+            assert np.allclose(ref[1], got[1], rtol=2e-6, atol=2e-6)
+        else:
+            assert all(np.array_equal(x, y) for x, y in zip(ref[0], got[0]))
+            assert np.array_equal(ref[1], got[1])
     b = load(tgf, Ls, fields, prec)
     best = tune.tune(b, eps=0.01, steps=3, path=str(tmp_path / "tune.json"))
-    assert best in tune.candidates()
+    assert best in tune.candidates(tgf.PRECISIONS[prec])
     assert all(np.array_equal(x, y) for x, y in zip(b.get_links(), fields)) or prec == "fp32"
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp32_r12"])
+def test_shared_corner_tile_matches_the_oracle(tgf, prec):
+    """Tile 3 (forward-staple corners passed between direction warps through shared memory) on
+    ragged boxes whose last block is partly past the configuration's end (those lanes take part
+    in the named barriers on site 0), twists in three planes: one RK3 step against the oracle on
+    every link, and a short flow against the oracle's records."""
+    from paper_2107_03747_gb300 import tune
+
+    tw = np.zeros((4, 4), dtype=np.int64)
+    for a, b_, k in [(0, 1, 1), (0, 3, 2), (1, 2, 1)]:
+        tw[a, b_], tw[b_, a] = k, -k
+    Ls = [(3, 3, 5, 7), (4, 4, 12, 12), (2, 3, 4, 5), (6, 6, 18, 18)]
+    fields = [I.random_links(L, 400 + i, 0.5) for i, L in enumerate(Ls)]
+    flags = tune.tune_flags(0, False, 3)
+    b = load(tgf, Ls, fields, prec, [tgf.twist6(tw)] * len(Ls))
+    obs, n = b.flow(0.02, 0.02, flags=flags)  # one step, no re-projection
+    got = b.get_links()
+    for i, U in enumerate(fields):
+        ref = O.rk3_step(U, 0.02, tw)
+        assert np.abs(got[i] - ref).max() < 5e-6, (Ls[i], np.abs(got[i] - ref).max())
+    b = load(tgf, Ls, fields, prec, [tgf.twist6(tw)] * len(Ls))
+    obs, n = b.flow(0.02, 0.08, flags=flags)
+    o = obs.cpu().numpy()
+    for i, U in enumerate(fields):
+        _, rec = O.flow(U, 0.02, 0.08, tw)
+        assert n[i] == len(rec)
+        for g, r in zip(o[i, : n[i]], rec):
+            assert g[1] == pytest.approx(r[1], rel=5e-6)
+            assert abs(g[2] - r[2]) < 2e-5
 
 
 def test_large_batch_uses_the_full_descriptor_and_matches_oracle(tgf):

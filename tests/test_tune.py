@@ -10,9 +10,17 @@ class FakeBatch:
 
 
 def test_candidates_cover_the_default_and_every_setting():
-    c = tune.candidates()
-    assert 0 in c and len(set(c)) == len(tune.GRIDS) * len(tune.ORDERS)
+    c = tune.candidates(1)
+    assert 0 in c and len(set(c)) == len(tune.GRIDS) * len(tune.ORDERS) * len(tune.TILES)
+    c64 = tune.candidates(0)
+    assert 0 in c64 and len(set(c64)) == len(tune.GRIDS) * len(tune.ORDERS)
+    assert all((f >> 13) & 3 == 0 for f in c64)  # FP64 has one tile
     assert tune.tune_flags(2, True) == (2 << 8) | (1 << 12)
+    assert tune.tune_flags(1, False, 2) == (1 << 8) | (2 << 13)
+    assert tune.flags_setting(tune.tune_flags(1, True, 1)) == {
+        "grid_k": 1, "size_order": True, "tile": 1, "sites_per_block": 64, "resident_blocks_per_sm": 2,
+        "shared_corners": False}
+    assert tune.flags_setting(tune.tune_flags(0, False, 3))["shared_corners"]
 
 
 def test_workload_key_ignores_member_order():
@@ -39,7 +47,7 @@ def test_tune_stores_and_reuses_the_winner(tmp_path):
     b = FakeBatch(1, [(8, 8, 24, 24)] * 16)
     best = tune.tune(b, path=path, timer=timer)
     assert best == tune.tune_flags(2, True)
-    assert sorted(calls) == sorted(tune.candidates())
+    assert sorted(calls) == sorted(tune.candidates(1))
     d = json.load(open(path))
     assert list(d.values())[0]["flags"] == best
     calls.clear()
