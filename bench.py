@@ -188,7 +188,7 @@ class Clocks:
                 "samples": len(rows), "reasons": reasons}
 
 
-STAGE_SOURCES = ["stage.cu", "su3.cuh", "expm.cuh", "lattice.cuh"]
+STAGE_SOURCES = ["stage_kernel.cuh", "stage.cu", "stage_tiles.cu", "su3.cuh", "expm.cuh", "lattice.cuh"]
 
 
 def stage_source_hash():
@@ -331,20 +331,21 @@ def run_reference(args):
 # GPU arm
 # ------------------------------------------------------------------------------------------------
 
-def time_stages(tgf, b, prec_name, nrep=10):
+def time_stages(tgf, b, prec_name, nrep=10, flags=0):
     """Mean device time (ms) of each RK3 stage kernel launch on `b` (CUDA events on the stream the
-    kernels are launched on) and of one measurement."""
+    kernels are launched on; `flags` selects the launch tile) and of one measurement."""
     import torch
 
     stream = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     out = {}
+    tile = flags & (0x7 << 13)
     for s in (1, 2, 3):
-        tgf.tgf_stage(b.prec, b.lat, b.links, b.links_tmp, b.accum, s, EPS, 0)
+        tgf.tgf_stage(b.prec, b.lat, b.links, b.links_tmp, b.accum, s, EPS, 0, tile)
         torch.cuda.synchronize()
         e0.record(stream)
         for _ in range(nrep):
-            tgf.tgf_stage(b.prec, b.lat, b.links, b.links_tmp, b.accum, s, EPS, 0)
+            tgf.tgf_stage(b.prec, b.lat, b.links, b.links_tmp, b.accum, s, EPS, 0, tile)
         e1.record(stream)
         torch.cuda.synchronize()
         out[s] = e0.elapsed_time(e1) / nrep
@@ -447,18 +448,12 @@ def profile_stages(args):
     b = tgf.FlowBatch(Ls, args.profile_stages)
     tgf.tgf_pack(b.prec, b.lat, canon, b.links)
     del canon
-    if args.tile is None:
-        for _ in range(args.steps):
-            for s in (1, 2, 3):
-                tgf.tgf_stage(b.prec, b.lat, b.links, b.links_tmp, b.accum, s, EPS, 0)
-    else:
-        # the flow's own launches with the given launch tile: one measured step first (stage 1 with
-        # the clover halves), then args.steps unmeasured steps; direct launches, no graph
-        from paper_2107_03747_gb300 import tune
+    from paper_2107_03747_gb300 import tune
 
-        obs = torch.zeros(len(Ls) * 4 * 5, dtype=torch.float64, device="cuda")
-        tgf.tgf_flow(b.prec, b.lat, b.links, b.links_tmp, b.accum, b.scratch, EPS, [EPS * (args.steps + 1)] * len(Ls),
-                     obs, 4, 10 ** 6, 0, tune.tune_flags(0, False, args.tile) | tgf.TGF_NO_GRAPH)
+    flags = tune.tune_flags(0, False, args.tile or 0)
+    for _ in range(args.steps):
+        for s in (1, 2, 3):
+            tgf.tgf_stage(b.prec, b.lat, b.links, b.links_tmp, b.accum, s, EPS, 0, flags)
     torch.cuda.synchronize()
     print(json.dumps({"profile_stages": args.profile_stages, "workload": args.workload, "tile": args.tile,
                       "launches": 3 * args.steps}))
@@ -493,7 +488,9 @@ def run_tgf(args):
 
     reunit = args.reunit if prec != tgf.TGF_FP64 else 0
     flags = 0
-    if args.tune:
+    if args.launch_flags is not None:
+        flags = args.launch_flags
+    elif args.tune:
         # launch settings of tgf_flow timed on this workload (results are the same for all of them)
         from paper_2107_03747_gb300 import tune
 
@@ -555,12 +552,14 @@ def run_tgf(args):
              "fp32_packed": tgf.tgf_fma_peak(tgf.TGF_FMA_PEAK_FP32X2)}
     hbm = hbm_peak_gbs()
     tgf.tgf_pack(prec, b.lat, canon_dev, b.links)
-    stage_ms, meas_ms = time_stages(tgf, b, args.prec)
+    stage_ms, meas_ms = time_stages(tgf, b, args.prec, flags=flags)
     roof = roofline_of(tgf, args.prec, V, stage_ms, meas_ms, args.workload, peaks, hbm)
+    roof["launch_tile"] = (flags >> 13) & 0x7
 
     # ---- the other precision forms on the same workload, and the FP64 reference flow ---------------
     forms = {}
     main_rec = {"value": value, "ms_per_step": ms, "roofline_frac": roof["frac"], "stage_ms": stage_ms,
+                "launch_tuning": tune_setting(flags) if prec != tgf.TGF_FP64 else None,
                 "stage_hbm_gbs": roof["hbm_gbs"], "traffic_per_launch": roof["traffic"],
                 "flow_hbm_gbs": flow_bytes(args.prec, members) / (ms * 1e-3) / 1e9,
                 "flow_bytes_per_step": flow_bytes(args.prec, members), "link_bytes": tgf.tgf_links_bytes(prec, b.lat)}
@@ -575,9 +574,19 @@ def run_tgf(args):
             bf = tgf.FlowBatch(Ls, pn, device=dev)
             of = torch.zeros_like(obs)
             ru = args.reunit if pn != "fp64" else 0
-            # FP64: one run with direct launches (no graph to capture, ~26 ms kernels); FP32-12: the
-            # first run captures the graph, the second is timed
-            fl = tgf.TGF_NO_GRAPH if pn == "fp64" else 0
+            # FP64: one run with direct launches (no graph to capture, ~26 ms kernels); FP32 forms:
+            # the launch setting tuned for this form, the first run captures the graph, the second
+            # is timed
+            fl = tgf.TGF_NO_GRAPH
+            if pn != "fp64":
+                fl = 0
+                if args.tune and args.launch_flags is None:
+                    from paper_2107_03747_gb300 import tune
+
+                    tgf.tgf_pack(bf.prec, bf.lat, canon_dev, bf.links)
+                    fl = tune.tune(bf, eps=EPS, steps=4, measure_every=1, force=True)
+                elif args.launch_flags is not None:
+                    fl = args.launch_flags
             for r in range(1 if pn == "fp64" else 2):
                 tgf.tgf_pack(bf.prec, bf.lat, canon_dev, bf.links)
                 torch.cuda.synchronize()
@@ -589,13 +598,14 @@ def run_tgf(args):
             msf = e0.elapsed_time(e1)
             oo = of.view(len(Ls), cap, 5).cpu().numpy()
             tgf.tgf_pack(bf.prec, bf.lat, canon_dev, bf.links)
-            sm, mm = time_stages(tgf, bf, pn, nrep=3 if pn == "fp64" else 10)
+            sm, mm = time_stages(tgf, bf, pn, nrep=3 if pn == "fp64" else 10, flags=fl & ~tgf.TGF_NO_GRAPH)
             rf = roofline_of(tgf, pn, V, sm, mm, args.workload, peaks, hbm)
             forms[pn] = {"value": work / (msf * 1e-3), "ms_per_step": msf, "roofline_frac": rf["frac"],
                          "stage_ms": sm, "stage_hbm_gbs": rf["hbm_gbs"], "traffic_per_launch": rf["traffic"],
                          "flow_hbm_gbs": flow_bytes(pn, members) / (msf * 1e-3) / 1e9,
                          "flow_bytes_per_step": flow_bytes(pn, members),
-                         "link_bytes": tgf.tgf_links_bytes(bf.prec, bf.lat), "_obs": oo, "_nrec": nr}
+                         "link_bytes": tgf.tgf_links_bytes(bf.prec, bf.lat), "_obs": oo, "_nrec": nr,
+                         "launch_tuning": tune_setting(fl & ~tgf.TGF_NO_GRAPH) if pn != "fp64" else None}
             if pn == "fp64":
                 o64 = oo
             del bf
@@ -659,7 +669,8 @@ def run_tgf(args):
                        "l2": ("inputs larger than L2" if link_bytes > L2_BYTES else "inputs smaller than L2") +
                              f" ({link_bytes / 1e6:.0f} MB links, {canon_bytes / 1e6:.0f} MB canonical)",
                        "parallelism": f"replicas x{ws}", "graph": True,
-                       "launch_tuning": dict(flags=flags, tuned=bool(args.tune), **tune_setting(flags))},
+                       "launch_tuning": dict(flags=flags, tuned=bool(args.tune and args.launch_flags is None),
+                                             **tune_setting(flags))},
             "e2e": {"value": e2e_value, "unit": "site-steps/s", "h2d_bytes_per_step": canon_bytes,
                     "d2h_bytes_per_step": obs_host.numel() * 8, "ms_per_step": ms_e2e},
             "gpu_launches": launches_per_flow(members) * args.steps,
@@ -758,12 +769,14 @@ def main():
     ap.add_argument("--no-tune", dest="tune", action="store_false",
                     help="use the default launch settings instead of timing the candidates first")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle timing")
+    ap.add_argument("--launch-flags", type=int, default=None,
+                    help="tgf_flow launch flags to use instead of tuning (reproduces a tuned run under a profiler)")
     ap.add_argument("--cpu-units", type=int, default=0,
                     help="oracle units in the cpu_baseline pool (default: one per host core, memory permitting)")
     ap.add_argument("--profile-stages", default=None, choices=list(PREC_NAMES),
                     help="only run the stage kernels of the workload in this precision (ncu traffic captures)")
-    ap.add_argument("--tile", type=int, default=None, choices=[0, 1, 2, 3],
-                    help="with --profile-stages: run the flow's launches with this launch tile")
+    ap.add_argument("--tile", type=int, default=None, choices=[0, 1, 2, 3, 4],
+                    help="with --profile-stages: launch the stage kernels with this launch tile")
     args = ap.parse_args()
     if args.cpu_units <= 0:
         args.cpu_units = os.cpu_count() or 1

@@ -107,13 +107,14 @@ typedef enum {
  * TGF_TUNE_SIZE_ORDER orders the configurations of each launch by size, largest first. */
 #define TGF_TUNE_GRID(k) (((unsigned)(k) & 0xFu) << 8)
 #define TGF_TUNE_SIZE_ORDER (1u << 12)
-/* TGF_TUNE_TILE(t): launch tile of the FP32 forms' stage kernels -- 0: 32 sites per block, one
- * warp per direction, up to 128 registers; 1: 64 sites per block (two warps per direction); 2: 32
- * sites per block with up to 168 registers (3 resident blocks per SM); 3: as 0, with the
- * forward-staple corners U_b(n+a) U_a(n+b)^+ of the unmeasured stages formed once per pair of
- * direction warps and passed through shared memory (results equal up to rounding).  Tiles 0-2
- * give bitwise the same flow.  Ignored in FP64. */
-#define TGF_TUNE_TILE(t) (((unsigned)(t) & 0x3u) << 13)
+/* TGF_TUNE_TILE(t): launch tile of the FP32 forms' stage kernels -- 0: 32 consecutive sites per
+ * block, one warp per direction; 1: 64 sites per block (two warps per direction); 2: 32 sites per
+ * block as a 4 x 2 x 2 x 2 hypercube (where L0 % 4 == 0 and L1, L2, L3 are even; consecutive
+ * sites otherwise); 3: as 0, with the forward-staple corners U_b(n+a) U_a(n+b)^+ of the
+ * unmeasured stages formed once per pair of direction warps and passed through shared memory;
+ * 4: as 2 with the shared corners of 3.  Tiles 0-2 give bitwise the same flow, 3 and 4 the same
+ * up to rounding.  Ignored in FP64. */
+#define TGF_TUNE_TILE(t) (((unsigned)(t) & 0x7u) << 13)
 
 typedef struct {
     int L[4];        /* extents, x0 fastest                                          */
@@ -174,9 +175,10 @@ tgf_status tgf_download(int prec, const tgf_lattice *lat, int ncfg, const void *
  * and w_out = exp(X) w_in (exact SU(3) exponential).  The three stages equal Luscher's
  * W1 = e^{Z0/4} W0, W2 = e^{8/9 Z1 - 17/36 Z0} W1, W3 = e^{3/4 Z2 - 8/9 Z1 + 17/36 Z0} W2.
  * w_in and w_out must not overlap.  reunit != 0 (stage 3, FP32 forms) re-projects w_out onto
- * SU(3) by Gram-Schmidt in FP64 before storing. */
+ * SU(3) by Gram-Schmidt in FP64 before storing.  flags: 0 or TGF_TUNE_TILE(t), the launch tile of
+ * the FP32 forms (as in tgf_flow). */
 tgf_status tgf_stage(int prec, const tgf_lattice *lat, int ncfg, const void *w_in, void *w_out,
-                     void *accum, int stage, double eps, int reunit, void *stream);
+                     void *accum, int stage, double eps, int reunit, unsigned flags, void *stream);
 
 /* Measure every configuration of `links` at flow time t: obs_dev[c * obs_stride + rec] receives
  * {t, E, Q, P, S} of configuration c.  `scratch` holds the per-block partial sums (size from

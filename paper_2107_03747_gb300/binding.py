@@ -57,7 +57,7 @@ _SIGS = {
     "tgf_unpack": [C.c_int, _LATP, C.c_int, _P, _P, _P],
     "tgf_upload": [C.c_int, _LATP, C.c_int, _P, _P, _SZ, _P, _P],
     "tgf_download": [C.c_int, _LATP, C.c_int, _P, _P, _SZ, _P, _P],
-    "tgf_stage": [C.c_int, _LATP, C.c_int, _P, _P, _P, C.c_int, C.c_double, C.c_int, _P],
+    "tgf_stage": [C.c_int, _LATP, C.c_int, _P, _P, _P, C.c_int, C.c_double, C.c_int, C.c_uint, _P],
     "tgf_measure": [C.c_int, _LATP, C.c_int, _P, _P, _SZ, _P, _SZ, C.c_int, C.c_double, C.c_uint, _P],
     "tgf_flow": [C.c_int, _LATP, C.c_int, _P, _P, _P, _P, _SZ, C.c_double, C.POINTER(C.c_double), C.c_int,
                  C.c_int, C.c_uint, _P, _SZ, C.POINTER(C.c_int), _P],
@@ -204,8 +204,8 @@ def tgf_download(prec, lat, links, staging, canon_host, stream=None):
                              staging.numel() * staging.element_size(), p, _stream(stream)))
 
 
-def tgf_stage(prec, lat, w_in, w_out, accum, stage, eps, reunit=0, stream=None):
-    _check(_lib.tgf_stage(prec, lat, len(lat), _ptr(w_in), _ptr(w_out), _ptr(accum), stage, eps, reunit,
+def tgf_stage(prec, lat, w_in, w_out, accum, stage, eps, reunit=0, flags=0, stream=None):
+    _check(_lib.tgf_stage(prec, lat, len(lat), _ptr(w_in), _ptr(w_out), _ptr(accum), stage, eps, reunit, flags,
                           _stream(stream)))
 
 
@@ -470,7 +470,7 @@ class FlowBatch:
 
     def stage(self, stage, eps, reunit=0, stream=None):
         """One RK3 stage from ``links`` into ``links_tmp``; then the two are swapped."""
-        tgf_stage(self.prec, self.lat, self.links, self.links_tmp, self.accum, stage, eps, reunit, stream)
+        tgf_stage(self.prec, self.lat, self.links, self.links_tmp, self.accum, stage, eps, reunit, 0, stream)
         self.links, self.links_tmp = self.links_tmp, self.links
 
     def flow(self, eps, t_end, measure_every=1, reunit_every=0, flags=0, stream=None, obs=None):

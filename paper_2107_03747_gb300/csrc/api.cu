@@ -430,7 +430,7 @@ tgf_status tgf_download(int prec, const tgf_lattice* lat, int ncfg, const void* 
 }
 
 tgf_status tgf_stage(int prec, const tgf_lattice* lat, int ncfg, const void* w_in, void* w_out, void* accum, int stage,
-                     double eps, int reunit, void* stream) {
+                     double eps, int reunit, unsigned flags, void* stream) {
     Range range_("tgf_stage");
     tgf_status s;
     if ((s = injected_badarg("tgf_stage"))) return s;
@@ -440,10 +440,13 @@ tgf_status tgf_stage(int prec, const tgf_lattice* lat, int ncfg, const void* w_i
     if (stage < 1 || stage > 3) return fail(TGF_EINVAL, "stage %d outside 1..3", stage);
     if (!(std::isfinite(eps)) || eps == 0.0) return fail(TGF_EINVAL, "eps = %g must be finite and non-zero", eps);
     if (w_in == w_out) return fail(TGF_EINVAL, "w_in and w_out must be distinct buffers");
+    if (flags & ~(0x7u << 13)) return fail(TGF_EINVAL, "tgf_stage: unknown flags 0x%x (only TGF_TUNE_TILE)", flags);
+    const int tile = prec == TGF_FP64 ? 0 : (int)((flags >> 13) & 0x7u);
+    if (tile >= kTiles) return fail(TGF_EINVAL, "tgf_stage: launch tile %d outside 0..%d", tile, kTiles - 1);
     Layout Ly = layout(prec, lat, ncfg);
-    Batch B = make_batch(lat, Ly, all_cfgs(ncfg), 32);
+    Batch B = make_batch(lat, Ly, all_cfgs(ncfg), tile_sites(tile));
     for (int i = 0; i < ncfg; ++i) B.c[i].h = eps;
-    launch_stage(prec, stage, 0, reunit, B, w_in, w_out, accum, nullptr, (cudaStream_t)stream);
+    launch_stage(prec, stage, 0, reunit, B, w_in, w_out, accum, nullptr, (cudaStream_t)stream, 0, tile);
     return last_launch("stage");
 }
 
@@ -861,12 +864,12 @@ static tgf_status enqueue_flow(int prec, const tgf_lattice* lat, int ncfg, const
         int dev = 0, sms = 0;
         TGF_CUDA(cudaGetDevice(&dev));
         TGF_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-        const unsigned t = (flags >> 13) & 0x3u;  // resident blocks per SM of the tile
-        grid = k * sms * (prec == TGF_FP64 ? 2 : t == 1 ? 2 : t == 2 ? 3 : 4);
+        const unsigned t = (flags >> 13) & 0x7u;  // resident blocks per SM of the tile
+        grid = k * sms * (prec == TGF_FP64 ? 2 : t == 1 ? 2 : 4);
     }
     const bool by_size = (flags & TGF_TUNE_SIZE_ORDER) != 0;
     // launch tile of the FP32 forms' stage kernels (FP64 has one tile)
-    const int tile = prec == TGF_FP64 ? 0 : (int)((flags >> 13) & 0x3u);
+    const int tile = prec == TGF_FP64 ? 0 : (int)((flags >> 13) & 0x7u);
     if (tile >= kTiles) return fail(TGF_EINVAL, "tgf_flow: launch tile %d outside 0..%d", tile, kTiles - 1);
     void* cur = w;
     void* alt = w_tmp;

@@ -356,7 +356,7 @@ void launch_stage(int prec, int stage, int mode, int reunit, const Batch& B, con
                   void* acc, void* clov, cudaStream_t st, int grid = 0, int tile = 0);
 void launch_stage_tile(int tile, int prec, int stage, int mode, int reunit, const Batch& B, const void* w_in,
                        void* w_out, void* acc, void* clov, cudaStream_t st, int grid);
-constexpr int kTiles = 4;
+constexpr int kTiles = 5;
 inline int tile_sites(int tile) { return tile == 1 ? 64 : 32; }
 void launch_clover_sum(int prec, unsigned flags, const Batch& B, const void* clov, double* partial,
                        cudaStream_t st);

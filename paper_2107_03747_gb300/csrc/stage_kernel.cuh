@@ -60,17 +60,40 @@ __device__ __forceinline__ void reunitarize(mat3<T>& u) {
 //      (at most 128 registers per thread), 2 in FP64
 //   1  64 sites per block, two warps per direction (a block spans two 32-site rows), 2 resident
 //      blocks of 256 threads per SM (at most 128 registers)
-//   2  32 sites per block with a looser register cap: 3 resident blocks per SM (at most 168
-//      registers), fewer warps but more room for loads in flight
+//   2  32 sites per block as a 4 x 2 x 2 x 2 hypercube (x0 x1 x2 x3) instead of 32 consecutive
+//      sites: a run of 4 sites along x0 is one full 128-byte line of a 32-byte plane, and more of
+//      the neighbours along x1, x2, x3 fall inside the block (used where L0 is a multiple of 4
+//      and L1, L2, L3 are even; other configurations of the launch keep the consecutive order)
 //   3  as 0, and in the unmeasured stages the block's direction warps share the forward-staple
 //      corners T_ab in pairs through shared memory (below)
-// Tiles 1 to 3 exist for the FP32 forms only.  Tiles 0-2 compute the same flow bit for bit; tile
-// 3 forms the shared staples as (Z T_ba)^+ U^+ instead of Z* T_ab U^+, equal up to rounding.
+//   4  as 2 (hypercube), with the shared corners of 3
+// Tiles 1 to 4 exist for the FP32 forms only.  Tiles 0-2 compute the same flow bit for bit; tiles
+// 3 and 4 form the shared staples as (Z T_ba)^+ U^+ instead of Z* T_ab U^+, equal up to rounding.
 template <int TILE>
 struct StageTile {
     static constexpr int spb = TILE == 1 ? 64 : 32;
-    static constexpr int minb32 = TILE == 1 ? 2 : TILE == 2 ? 3 : 4;  // tiles 0 and 3: 4
+    static constexpr int minb32 = TILE == 1 ? 2 : 4;
+    static constexpr bool cube = TILE == 2 || TILE == 4;
+    static constexpr bool pair = TILE == 3 || TILE == 4;
 };
+
+// Site of lane `lane` in block `b` (index within its configuration) of a hypercube tile: the
+// block's origin (4 h0, 2 h1, 2 h2, 2 h3) from the multiply-shift constants of the fine strides,
+// floor(b / (L0/4)) = floor(4b / L0) etc. (exact: L0/4, L1/2, L2/2 are integers); lanes cover
+// dx0 = lane & 3, dx1..dx3 = the next three bits.  Returns false if the extents do not allow it.
+__device__ __forceinline__ bool cube_site(const CfgDesc& c, int b, int lane, int& s, int (&x)[4]) {
+    if ((c.L[0] & 3) | (c.L[1] & 1) | (c.L[2] & 1) | (c.L[3] & 1)) return false;
+    const unsigned u = (unsigned)b;
+    const int q1 = (int)(__umulhi(u << 6, c.dmul[0]) >> c.dsh[0]);  // b / (L0/4)
+    const int q2 = (int)(__umulhi(u << 7, c.dmul[1]) >> c.dsh[1]);  // b / (L0 L1/8)
+    const int q3 = (int)(__umulhi(u << 8, c.dmul[2]) >> c.dsh[2]);  // b / (L0 L1 L2/16)
+    x[0] = 4 * (b - q1 * (c.L[0] >> 2)) + (lane & 3);
+    x[1] = 2 * (q1 - q2 * (c.L[1] >> 1)) + ((lane >> 2) & 1);
+    x[2] = 2 * (q2 - q3 * (c.L[2] >> 1)) + ((lane >> 3) & 1);
+    x[3] = 2 * q3 + (lane >> 4);
+    s = x[0] + x[1] * c.st[1] + x[2] * c.st[2] + x[3] * c.st[3];
+    return true;
+}
 
 // Tile 3: forward-staple corners shared in pairs.  T_ab(n) = U_b(n+a) U_a(n+b)^+ serves link (n, a)
 // (staple T_ab U_b(n)^+) and link (n, b) (staple T_ab^+ U_a(n)^+ = T_ba U_a(n)^+), so of the two
@@ -150,17 +173,19 @@ k_stage(const __grid_constant__ BatchT<CAP> B, const typename Store<P>::T* __res
     // tile 3 (FP32 forms, unmeasured stages): corners shared in pairs; every lane of the block's four
     // warps takes part in the named barriers, lanes past the configuration's end on site 0 with
     // their results discarded
-    constexpr bool PAIR = (P != P64) && TILE == 3 && MODE == 0;
+    constexpr bool PAIR = (P != P64) && StageTile<TILE>::pair && MODE == 0;
     __shared__ cx<T> sP[PAIR ? 6 : 1][9][32];
 
     for (int blk = blockIdx.x; blk < B.nblk; blk += gridDim.x) {
         const int ci = find_cfg(B, blk);
         const CfgDesc& c = B.c[ci];
-        const int s_raw = (blk - c.blk0) * SPB + row * 32 + lane;
+        int s_raw = (blk - c.blk0) * SPB + row * 32 + lane;
+        int xc[4];
+        bool have_x = false;
+        if constexpr (StageTile<TILE>::cube) have_x = cube_site(c, blk - c.blk0, lane, s_raw, xc);
         const bool valid = s_raw < c.V;
         const int s = (PAIR && !valid) ? 0 : s_raw;
-        int xc[4];
-        site_coords(c, valid ? s : 0, xc);
+        if (!have_x) site_coords(c, valid ? s : 0, xc);
         const unsigned eb = edge_bits(c, xc);  // boundary flags (lattice.cuh)
         const int Vp = c.Vp;
         const T* base = w_in + c.w_off;

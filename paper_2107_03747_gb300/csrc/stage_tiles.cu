@@ -12,9 +12,12 @@ void launch_stage_tile(int tile, int prec, int stage, int mode, int reunit, cons
     } else if (tile == 2) {
         if (prec == P32) launch_stage_p<P32, 2>(stage, mode, reunit, B, w_in, w_out, acc, clov, st, grid);
         else launch_stage_p<P32R12, 2>(stage, mode, reunit, B, w_in, w_out, acc, clov, st, grid);
-    } else {
+    } else if (tile == 3) {
         if (prec == P32) launch_stage_p<P32, 3>(stage, mode, reunit, B, w_in, w_out, acc, clov, st, grid);
         else launch_stage_p<P32R12, 3>(stage, mode, reunit, B, w_in, w_out, acc, clov, st, grid);
+    } else {
+        if (prec == P32) launch_stage_p<P32, 4>(stage, mode, reunit, B, w_in, w_out, acc, clov, st, grid);
+        else launch_stage_p<P32R12, 4>(stage, mode, reunit, B, w_in, w_out, acc, clov, st, grid);
     }
 }
 

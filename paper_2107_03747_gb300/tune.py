@@ -18,24 +18,25 @@ from collections import Counter
 
 GRIDS = (0, 1, 2, 4)
 ORDERS = (False, True)
-# launch tiles of the FP32 forms' stage kernels (tgf.h TGF_TUNE_TILE): 32 sites per block with up
-# to 128 registers, 64 sites per block (two warps per direction), 32 sites with up to 168 registers,
-# 32 sites with the forward-staple corners shared in pairs of direction warps
-TILES = (0, 1, 2, 3)
+# launch tiles of the FP32 forms' stage kernels (tgf.h TGF_TUNE_TILE): 32 consecutive sites per
+# block, 64 sites per block (two warps per direction), 32 sites as a 4x2x2x2 hypercube, and the
+# first and third with the forward-staple corners shared in pairs of direction warps
+TILES = (0, 1, 2, 3, 4)
 TGF_TUNE_SIZE_ORDER = 1 << 12
 TGF_FP64 = 0
 
 
 def tune_flags(grid: int, by_size: bool, tile: int = 0) -> int:
-    return ((grid & 0xF) << 8) | (TGF_TUNE_SIZE_ORDER if by_size else 0) | ((tile & 0x3) << 13)
+    return ((grid & 0xF) << 8) | (TGF_TUNE_SIZE_ORDER if by_size else 0) | ((tile & 0x7) << 13)
 
 
 def flags_setting(flags: int) -> dict:
     """The launch setting a flags word selects (reported next to bench numbers)."""
-    return {"grid_k": (flags >> 8) & 0xF, "size_order": bool(flags & TGF_TUNE_SIZE_ORDER),
-            "tile": (flags >> 13) & 0x3, "sites_per_block": 64 if (flags >> 13) & 0x3 == 1 else 32,
-            "resident_blocks_per_sm": {0: 4, 1: 2, 2: 3, 3: 4}[(flags >> 13) & 0x3],
-            "shared_corners": (flags >> 13) & 0x3 == 3}
+    tile = (flags >> 13) & 0x7
+    return {"grid_k": (flags >> 8) & 0xF, "size_order": bool(flags & TGF_TUNE_SIZE_ORDER), "tile": tile,
+            "sites_per_block": 64 if tile == 1 else 32, "resident_blocks_per_sm": 2 if tile == 1 else 4,
+            "site_order": "4x2x2x2 hypercube" if tile in (2, 4) else "consecutive",
+            "shared_corners": tile in (3, 4)}
 
 
 def candidates(prec: int | None = None):

@@ -78,7 +78,7 @@ def test_injected_bad_argument_fault(lib, monkeypatch):
     monkeypatch.setenv("TGF_FAULT", "badarg")
     s = lib._lib.tgf_flow(0, lat, 1, a, 2 * a, 3 * a, 4 * a, sb, 0.01, te, 1, 0, 0, 5 * a, 100, nrec, None)
     assert s == lib.TGF_EINVAL and b"TGF_FAULT=badarg" in lib._lib.tgf_last_error()
-    s = lib._lib.tgf_stage(0, lat, 1, a, 2 * a, 3 * a, 1, 0.01, 0, None)
+    s = lib._lib.tgf_stage(0, lat, 1, a, 2 * a, 3 * a, 1, 0.01, 0, 0, None)
     assert s == lib.TGF_EINVAL and b"TGF_FAULT=badarg" in lib._lib.tgf_last_error()
     monkeypatch.delenv("TGF_FAULT")
     s = lib._lib.tgf_flow(0, lat, 1, a, 2 * a, 3 * a, 4 * a, sb, 0.01, te, 1, 0, 0, 5 * a, 3, nrec, None)
@@ -181,7 +181,7 @@ def test_bad_arguments_are_rejected_before_device_work(lib, bad):
     elif bad == "same":
         args["w_out"] = ok
     s = lib._lib.tgf_stage(args["prec"], args["lat"], args["n"], args["w_in"], args["w_out"], args["acc"],
-                           args["stage"], args["eps"], 0, None)
+                           args["stage"], args["eps"], 0, 0, None)
     assert s == lib.TGF_EINVAL
     assert len(lib._lib.tgf_last_error()) > 0
 
@@ -312,3 +312,34 @@ def test_multiply_shift_division_reading_is_exact():
         n = [int(v) for v in n if 0 <= v < 2 ** 28]
         for v in n:
             assert (((v << 4) * m) >> 32) >> sh == v // d, (d, v)
+
+
+def test_hypercube_block_order_covers_every_site_once():
+    """The hypercube launch tile gives block b the origin (4 h0, 2 h1, 2 h2, 2 h3) with
+    h = (b mod L0/4, floor(4b/L0) mod L1/2, floor(8b/(L0 L1)) mod L2/2, floor(16b/(L0 L1 L2))), the
+    divisions by the multiply-shift constants of the site strides, and lanes the offsets
+    (lane & 3, bit 2, bit 3, bit 4): every site of every admissible box exactly once, in bounds."""
+    def magic(d):
+        sh = (d - 1).bit_length()
+        return ((1 << (28 + sh)) + d - 1) // d, sh
+
+    def div(n, mg):
+        return ((((n << 4) * mg[0]) >> 32) >> mg[1])
+
+    for L in [(4, 4, 12, 12), (8, 8, 24, 24), (12, 12, 36, 36), (16, 16, 48, 48), (8, 4, 6, 2), (4, 2, 2, 2)]:
+        st = [1, L[0], L[0] * L[1], L[0] * L[1] * L[2]]
+        mg = [magic(st[1]), magic(st[2]), magic(st[3])]
+        V = st[3] * L[3]
+        b = np.arange(V // 32, dtype=np.int64)
+        q1 = np.array([div(4 * int(v), mg[0]) for v in b])
+        q2 = np.array([div(8 * int(v), mg[1]) for v in b])
+        q3 = np.array([div(16 * int(v), mg[2]) for v in b])
+        lane = np.arange(32)
+        x0 = 4 * (b - q1 * (L[0] // 4))[:, None] + (lane & 3)
+        x1 = 2 * (q1 - q2 * (L[1] // 2))[:, None] + ((lane >> 2) & 1)
+        x2 = 2 * (q2 - q3 * (L[2] // 2))[:, None] + ((lane >> 3) & 1)
+        x3 = (2 * q3)[:, None] + (lane >> 4)
+        for x, n in zip((x0, x1, x2, x3), L):
+            assert x.min() >= 0 and x.max() < n
+        s = (x0 + x1 * st[1] + x2 * st[2] + x3 * st[3]).ravel()
+        assert np.array_equal(np.sort(s), np.arange(V))

@@ -526,20 +526,22 @@ def test_launch_tuning_settings_give_identical_flows(tgf, prec, tmp_path):
     assert all(np.array_equal(x, y) for x, y in zip(b.get_links(), fields)) or prec == "fp32"
 
 
+@pytest.mark.parametrize("tile", [2, 3, 4])
 @pytest.mark.parametrize("prec", ["fp32", "fp32_r12"])
-def test_shared_corner_tile_matches_the_oracle(tgf, prec):
-    """Tile 3 (forward-staple corners passed between direction warps through shared memory) on
-    ragged boxes whose last block is partly past the configuration's end (those lanes take part
-    in the named barriers on site 0), twists in three planes: one RK3 step against the oracle on
-    every link, and a short flow against the oracle's records."""
+def test_launch_tiles_match_the_oracle(tgf, prec, tile):
+    """Tiles 2-4 (hypercube site order, forward-staple corners passed between direction warps
+    through shared memory, both) on ragged boxes, some with a last block partly past the
+    configuration's end (those lanes take part in the named barriers on site 0), some with the
+    hypercube order (4x4x12x12, 8x4x6x2) and some without, twists in three planes: one RK3 step
+    against the oracle on every link, and a short flow against the oracle's records."""
     from paper_2107_03747_gb300 import tune
 
     tw = np.zeros((4, 4), dtype=np.int64)
     for a, b_, k in [(0, 1, 1), (0, 3, 2), (1, 2, 1)]:
         tw[a, b_], tw[b_, a] = k, -k
-    Ls = [(3, 3, 5, 7), (4, 4, 12, 12), (2, 3, 4, 5), (6, 6, 18, 18)]
+    Ls = [(3, 3, 5, 7), (4, 4, 12, 12), (2, 3, 4, 5), (6, 6, 18, 18), (8, 4, 6, 2)]
     fields = [I.random_links(L, 400 + i, 0.5) for i, L in enumerate(Ls)]
-    flags = tune.tune_flags(0, False, 3)
+    flags = tune.tune_flags(0, False, tile)
     b = load(tgf, Ls, fields, prec, [tgf.twist6(tw)] * len(Ls))
     obs, n = b.flow(0.02, 0.02, flags=flags)  # one step, no re-projection
     got = b.get_links()

@@ -17,10 +17,13 @@ def test_candidates_cover_the_default_and_every_setting():
     assert all((f >> 13) & 3 == 0 for f in c64)  # FP64 has one tile
     assert tune.tune_flags(2, True) == (2 << 8) | (1 << 12)
     assert tune.tune_flags(1, False, 2) == (1 << 8) | (2 << 13)
+    assert tune.tune_flags(0, False, 4) == 4 << 13
     assert tune.flags_setting(tune.tune_flags(1, True, 1)) == {
         "grid_k": 1, "size_order": True, "tile": 1, "sites_per_block": 64, "resident_blocks_per_sm": 2,
-        "shared_corners": False}
+        "site_order": "consecutive", "shared_corners": False}
     assert tune.flags_setting(tune.tune_flags(0, False, 3))["shared_corners"]
+    s4 = tune.flags_setting(tune.tune_flags(0, False, 4))
+    assert s4["shared_corners"] and s4["site_order"] == "4x2x2x2 hypercube"
 
 
 def test_workload_key_ignores_member_order():
