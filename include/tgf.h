@@ -108,12 +108,12 @@ typedef enum {
 #define TGF_TUNE_GRID(k) (((unsigned)(k) & 0xFu) << 8)
 #define TGF_TUNE_SIZE_ORDER (1u << 12)
 /* TGF_TUNE_TILE(t): launch tile of the FP32 forms' stage kernels -- 0: 32 consecutive sites per
- * block, one warp per direction; 1: 64 sites per block (two warps per direction); 2: 32 sites per
- * block as a 4 x 2 x 2 x 2 hypercube (where L0 % 4 == 0 and L1, L2, L3 are even; consecutive
- * sites otherwise); 3: as 0, with the forward-staple corners U_b(n+a) U_a(n+b)^+ of the
- * unmeasured stages formed once per pair of direction warps and passed through shared memory;
- * 4: as 2 with the shared corners of 3.  Tiles 0-2 give bitwise the same flow, 3 and 4 the same
- * up to rounding.  Ignored in FP64. */
+ * block, one warp per direction, 4 blocks per SM; 1: 64 sites per block (two warps per
+ * direction); 2: 32 sites per block as a 4 x 2 x 2 x 2 hypercube (where L0 % 4 == 0 and L1, L2,
+ * L3 are even; consecutive sites otherwise); 3: as 0, with the forward-staple corners
+ * U_b(n+a) U_a(n+b)^+ of the unmeasured stages formed once per pair of direction warps and passed
+ * through shared memory; 4: as 0 with 5 blocks per SM in the unmeasured stages (tighter register
+ * cap).  Tiles 0, 1, 2, 4 give bitwise the same flow, 3 the same up to rounding.  Ignored in FP64. */
 #define TGF_TUNE_TILE(t) (((unsigned)(t) & 0x7u) << 13)
 
 typedef struct {

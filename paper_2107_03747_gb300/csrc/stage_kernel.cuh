@@ -66,15 +66,17 @@ __device__ __forceinline__ void reunitarize(mat3<T>& u) {
 //      and L1, L2, L3 are even; other configurations of the launch keep the consecutive order)
 //   3  as 0, and in the unmeasured stages the block's direction warps share the forward-staple
 //      corners T_ab in pairs through shared memory (below)
-//   4  as 2 (hypercube), with the shared corners of 3
-// Tiles 1 to 4 exist for the FP32 forms only.  Tiles 0-2 compute the same flow bit for bit; tiles
-// 3 and 4 form the shared staples as (Z T_ba)^+ U^+ instead of Z* T_ab U^+, equal up to rounding.
+//   4  as 0 with a tighter register cap in the unmeasured stages: 5 resident blocks per SM (at
+//      most 102 registers; the measured stage 1 keeps 4), more warps to cover latency
+// Tiles 1 to 4 exist for the FP32 forms only.  Tiles 0, 1, 2 and 4 compute the same flow bit for
+// bit; tile 3 forms the shared staples as (Z T_ba)^+ U^+ instead of Z* T_ab U^+, equal up to
+// rounding.
 template <int TILE>
 struct StageTile {
     static constexpr int spb = TILE == 1 ? 64 : 32;
-    static constexpr int minb32 = TILE == 1 ? 2 : 4;
-    static constexpr bool cube = TILE == 2 || TILE == 4;
-    static constexpr bool pair = TILE == 3 || TILE == 4;
+    static constexpr int minb32 = TILE == 1 ? 2 : TILE == 4 ? 5 : 4;
+    static constexpr bool cube = TILE == 2;
+    static constexpr bool pair = TILE == 3;
 };
 
 // Site of lane `lane` in block `b` (index within its configuration) of a hypercube tile: the
@@ -114,8 +116,11 @@ __device__ __forceinline__ void bar_arrive(int id, int nthreads) {
 __device__ __forceinline__ void bar_sync(int id, int nthreads) {
     asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
 }
-template <int P, int TILE>
-constexpr int stage_min_blocks() { return P == P64 ? 2 : StageTile<TILE>::minb32; }
+// the measured stage 1 (MODE 1: clover halves too) needs more registers: at most 4 blocks per SM
+template <int P, int TILE, int MODE>
+constexpr int stage_min_blocks() {
+    return P == P64 ? 2 : (MODE != 0 && StageTile<TILE>::minb32 > 4) ? 4 : StageTile<TILE>::minb32;
+}
 
 // Plane index of (mu, nu), mu < nu, in the order 01, 23, 02, 13, 03, 12 (consecutive planes
 // pair up in the topological charge); -1 for mu >= nu.
@@ -151,7 +156,7 @@ __device__ __forceinline__ void store_ah(T* __restrict__ p, int Vp, int s, const
 // Thread (n, mu) writes D1 - D1^+ to site n and D2 - D2^+ to site n + mu for the planes its warp
 // builds (c_clover_owner), plus 3 - Re Tr(U F) (the twisted plaquette at n).
 template <int P, int STAGE, int MODE, int TILE, int CAP>
-__global__ void __launch_bounds__(4 * StageTile<TILE>::spb, (stage_min_blocks<P, TILE>()))
+__global__ void __launch_bounds__(4 * StageTile<TILE>::spb, (stage_min_blocks<P, TILE, MODE>()))
 k_stage(const __grid_constant__ BatchT<CAP> B, const typename Store<P>::T* __restrict__ w_in,
         typename Store<P>::T* __restrict__ w_out, typename Store<P>::T* __restrict__ acc,
         typename Store<P>::T* __restrict__ clov, int reunit) {

@@ -19,8 +19,8 @@ from collections import Counter
 GRIDS = (0, 1, 2, 4)
 ORDERS = (False, True)
 # launch tiles of the FP32 forms' stage kernels (tgf.h TGF_TUNE_TILE): 32 consecutive sites per
-# block, 64 sites per block (two warps per direction), 32 sites as a 4x2x2x2 hypercube, and the
-# first and third with the forward-staple corners shared in pairs of direction warps
+# block, 64 sites per block (two warps per direction), 32 sites as a 4x2x2x2 hypercube, the first
+# with the forward-staple corners shared in pairs of direction warps, the first with 5 blocks per SM
 TILES = (0, 1, 2, 3, 4)
 TGF_TUNE_SIZE_ORDER = 1 << 12
 TGF_FP64 = 0
@@ -34,9 +34,10 @@ def flags_setting(flags: int) -> dict:
     """The launch setting a flags word selects (reported next to bench numbers)."""
     tile = (flags >> 13) & 0x7
     return {"grid_k": (flags >> 8) & 0xF, "size_order": bool(flags & TGF_TUNE_SIZE_ORDER), "tile": tile,
-            "sites_per_block": 64 if tile == 1 else 32, "resident_blocks_per_sm": 2 if tile == 1 else 4,
-            "site_order": "4x2x2x2 hypercube" if tile in (2, 4) else "consecutive",
-            "shared_corners": tile in (3, 4)}
+            "sites_per_block": 64 if tile == 1 else 32,
+            "resident_blocks_per_sm": 2 if tile == 1 else 5 if tile == 4 else 4,
+            "site_order": "4x2x2x2 hypercube" if tile == 2 else "consecutive",
+            "shared_corners": tile == 3}
 
 
 def candidates(prec: int | None = None):

@@ -529,11 +529,11 @@ def test_launch_tuning_settings_give_identical_flows(tgf, prec, tmp_path):
 @pytest.mark.parametrize("tile", [2, 3, 4])
 @pytest.mark.parametrize("prec", ["fp32", "fp32_r12"])
 def test_launch_tiles_match_the_oracle(tgf, prec, tile):
-    """Tiles 2-4 (hypercube site order, forward-staple corners passed between direction warps
-    through shared memory, both) on ragged boxes, some with a last block partly past the
-    configuration's end (those lanes take part in the named barriers on site 0), some with the
-    hypercube order (4x4x12x12, 8x4x6x2) and some without, twists in three planes: one RK3 step
-    against the oracle on every link, and a short flow against the oracle's records."""
+    """Tiles 2-4 (hypercube site order; forward-staple corners passed between direction warps
+    through shared memory; a tighter register cap) on ragged boxes, some with a last block partly
+    past the configuration's end (those lanes take part in the named barriers on site 0), some
+    with the hypercube order (4x4x12x12, 8x4x6x2) and some without, twists in three planes: one
+    RK3 step against the oracle on every link, and a short flow against the oracle's records."""
     from paper_2107_03747_gb300 import tune
 
     tw = np.zeros((4, 4), dtype=np.int64)

@@ -22,8 +22,9 @@ def test_candidates_cover_the_default_and_every_setting():
         "grid_k": 1, "size_order": True, "tile": 1, "sites_per_block": 64, "resident_blocks_per_sm": 2,
         "site_order": "consecutive", "shared_corners": False}
     assert tune.flags_setting(tune.tune_flags(0, False, 3))["shared_corners"]
+    assert tune.flags_setting(tune.tune_flags(0, False, 2))["site_order"] == "4x2x2x2 hypercube"
     s4 = tune.flags_setting(tune.tune_flags(0, False, 4))
-    assert s4["shared_corners"] and s4["site_order"] == "4x2x2x2 hypercube"
+    assert not s4["shared_corners"] and s4["resident_blocks_per_sm"] == 5
 
 
 def test_workload_key_ignores_member_order():
