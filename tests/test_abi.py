@@ -343,3 +343,18 @@ def test_hypercube_block_order_covers_every_site_once():
             assert x.min() >= 0 and x.max() < n
         s = (x0 + x1 * st[1] + x2 * st[2] + x3 * st[3]).ravel()
         assert np.array_equal(np.sort(s), np.arange(V))
+
+
+def test_batch_and_lattice_limits(lib):
+    """TGF_MAX_CFG configurations are accepted, one more is refused; a box of more than 2^28 sites
+    (the limit of the multiply-shift coordinates) is refused, the largest admissible one accepted."""
+    n = C.c_size_t()
+    full = lib.lattices([(2, 2, 6, 6)] * lib.TGF_MAX_CFG)
+    assert lib._lib.tgf_links_bytes(1, full, lib.TGF_MAX_CFG, C.byref(n)) == lib.TGF_OK
+    over = lib.lattices([(2, 2, 6, 6)] * (lib.TGF_MAX_CFG + 1))
+    assert lib._lib.tgf_links_bytes(1, over, lib.TGF_MAX_CFG + 1, C.byref(n)) == lib.TGF_EINVAL
+    assert lib._lib.tgf_links_bytes(1, full, 0, C.byref(n)) == lib.TGF_EINVAL
+    # 9 l^4 <= 2^28 holds up to l = 73
+    assert lib._lib.tgf_links_bytes(1, lib.lattices([(73, 73, 219, 219)]), 1, C.byref(n)) == lib.TGF_OK
+    assert lib._lib.tgf_links_bytes(1, lib.lattices([(74, 74, 222, 222)]), 1, C.byref(n)) == lib.TGF_EINVAL
+    assert b"2^28" in lib._lib.tgf_last_error()

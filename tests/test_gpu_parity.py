@@ -573,3 +573,20 @@ def test_large_batch_uses_the_full_descriptor_and_matches_oracle(tgf):
         ref = O.rk3_step(fields[i], 0.02, TW)
         assert np.abs(got[i] - ref).max() <= 1e-12
         close_obs(m[i], O.measure(ref, TW))
+
+
+def test_a_full_256_configuration_batch_flows_like_the_oracle(tgf):
+    """The largest batch, TGF_MAX_CFG = 256 configurations of three box sizes and end times in one
+    FP32 flow (one CUDA graph): four of them, one per size and the last, against the oracle."""
+    Ls = [[(2, 2, 6, 6), (4, 4, 12, 12), (3, 3, 9, 9)][i % 3] for i in range(tgf.TGF_MAX_CFG)]
+    t_end = [[0.03, 0.02, 0.025][i % 3] for i in range(tgf.TGF_MAX_CFG)]
+    fields = [I.random_links(L, 500 + i, 0.4) for i, L in enumerate(Ls)]
+    b = load(tgf, Ls, fields, "fp32")
+    obs, n = b.flow(0.01, t_end)
+    o = obs.cpu().numpy()
+    for i in (0, 1, 2, tgf.TGF_MAX_CFG - 1):
+        _, rec = O.flow(fields[i], 0.01, t_end[i], TW)
+        assert n[i] == len(rec)
+        for g, r in zip(o[i, : n[i]], rec):
+            assert g[1] == pytest.approx(r[1], rel=2e-6)
+            assert abs(g[2] - r[2]) < 2e-5
