@@ -171,8 +171,8 @@ k_stage(const __grid_constant__ BatchT<CAP> B, const typename Store<P>::T* __res
     // T_{ab}(n) = U_b(n+a) U_a(n+b)^+ of the six planes a < b: the forward staple of link (n, a) in
     // direction b is T_ab U_b(n)^+, that of link (n, b) in direction a is T_ab^+ U_a(n)^+, so in
     // FP64 (bound by the FP64 pipe) each is computed once per site by one warp of the block and
-    // shared (42 instead of 48 staple products per site).  The FP32 forms are bound by instruction
-    // issue and latency, where the barrier costs more than the saved products: they recompute.
+    // shared behind one block barrier (42 instead of 48 staple products per site).  The FP32 forms,
+    // bound by latency, share them only in launch tile 3, in pairs of warps without a block barrier.
     constexpr bool SHARE = (P == P64);
     __shared__ cx<T> sT[SHARE ? 6 : 1][9][32];
     // tile 3 (FP32 forms, unmeasured stages): corners shared in pairs; every lane of the block's four
@@ -199,28 +199,29 @@ k_stage(const __grid_constant__ BatchT<CAP> B, const typename Store<P>::T* __res
         // row, the product's rows 0 and 1 are formed and its row 2 is rebuilt once (an SU(3)
         // product), which saves rebuilding that factor's row on load.
         constexpr bool TWO_ROW = (P == P32R12);
-        auto prod_nd = [&](mat3<T>& c, int da, int sa, int db, int sb, mat3<T>& fa, mat3<T>& fb) {
+        // out = U_da(sa) U_db(sb)^+ (prod_nd) or U_da(sa) U_db(sb) (prod_nn); fa, fb receive the factors
+        auto prod_nd = [&](mat3<T>& out, int da, int sa, int db, int sb, mat3<T>& fa, mat3<T>& fb) {
             if constexpr (TWO_ROW) {
                 Store<P32R12>::load_top(base + (size_t)da * R * Vp, Vp, sa, fa);
                 link(db, sb, fb);
-                mul_nd_top(c, fa, fb);
-                rebuild_row2(c);
+                mul_nd_top(out, fa, fb);
+                rebuild_row2(out);
             } else {
                 link(da, sa, fa);
                 link(db, sb, fb);
-                mul_nd(c, fa, fb);
+                mul_nd(out, fa, fb);
             }
         };
-        auto prod_nn = [&](mat3<T>& c, int da, int sa, int db, int sb, mat3<T>& fa, mat3<T>& fb) {
+        auto prod_nn = [&](mat3<T>& out, int da, int sa, int db, int sb, mat3<T>& fa, mat3<T>& fb) {
             if constexpr (TWO_ROW) {
                 Store<P32R12>::load_top(base + (size_t)da * R * Vp, Vp, sa, fa);
                 link(db, sb, fb);
-                mul_nn_top(c, fa, fb);
-                rebuild_row2(c);
+                mul_nn_top(out, fa, fb);
+                rebuild_row2(out);
             } else {
                 link(da, sa, fa);
                 link(db, sb, fb);
-                mul_nn(c, fa, fb);
+                mul_nn(out, fa, fb);
             }
         };
         mat3<T> sig, a, b, t;

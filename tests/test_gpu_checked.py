@@ -32,6 +32,17 @@ for prec in ("fp64", "fp32", "fp32_r12"):
     b.slices(3)
     b.get_links()
     assert tgf.tgf_check_errors() == 0, prec
+# every launch tile of the FP32 forms, on boxes with and without the hypercube order and with
+# partly filled last blocks
+from paper_2107_03747_gb300 import tune
+Lt = [(4, 4, 12, 12), (3, 3, 5, 7), (8, 4, 6, 2), (6, 6, 18, 18)]
+ft = [I.random_links(L, 30 + i, 0.5) for i, L in enumerate(Lt)]
+for prec in ("fp32", "fp32_r12"):
+    for tile in tune.TILES:
+        b = tgf.FlowBatch(Lt, prec, any_extents=True)
+        b.set_links(ft)
+        b.flow(0.01, [0.03, 0.02, 0.04, 0.01], measure_every=2, flags=tune.tune_flags(1 if tile == 3 else 0, False, tile))
+        assert tgf.tgf_check_errors() == 0, (prec, tile)
 Lm = [(4, 4, 12, 12), (2, 2, 6, 6)]
 m = tgf.FlowBatch(Lm, "fp64")
 m.set_links([I.random_links(L, 3, 0.5) for L in Lm])
