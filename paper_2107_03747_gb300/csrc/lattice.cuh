@@ -341,6 +341,54 @@ struct AccStore<float> {
     }
 };
 
+// The anti-Hermitian part D - D^+ of a 3x3 matrix as 9 reals {2 Im D_00, 2 Im D_11, 2 Im D_22,
+// (D_01 - conj D_10) re/im, (D_02 - conj D_20) re/im, (D_12 - conj D_21) re/im} in the clover
+// scratch: reals 0-7 as one 8-real vector per site (32 B in FP32, two 32-byte halves in FP64),
+// real 8 in a plane of its own; a slot takes 9 Vp reals.
+template <class T>
+struct AhStore;
+
+template <>
+struct AhStore<float> {
+    static __device__ __forceinline__ void store(float* __restrict__ base, int Vp, int s, const float (&v)[9]) {
+        s = checked_site(s, Vp);
+        const float a[8] = {v[0], v[1], v[2], v[3], v[4], v[5], v[6], v[7]};
+        st8(base + (size_t)s * 8, a);
+        base[(size_t)8 * Vp + s] = v[8];
+    }
+    static __device__ __forceinline__ void load(const float* __restrict__ base, int Vp, int s, float (&v)[9]) {
+        s = checked_site(s, Vp);
+        float a[8];
+        ld8_nc(base + (size_t)s * 8, a);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) v[k] = a[k];
+        v[8] = __ldg(base + (size_t)8 * Vp + s);
+    }
+};
+
+template <>
+struct AhStore<double> {
+    static __device__ __forceinline__ void store(double* __restrict__ base, int Vp, int s, const double (&v)[9]) {
+        s = checked_site(s, Vp);
+        const double a[4] = {v[0], v[1], v[2], v[3]}, b[4] = {v[4], v[5], v[6], v[7]};
+        st4d(base + (size_t)s * 8, a);
+        st4d(base + (size_t)s * 8 + 4, b);
+        base[(size_t)8 * Vp + s] = v[8];
+    }
+    static __device__ __forceinline__ void load(const double* __restrict__ base, int Vp, int s, double (&v)[9]) {
+        s = checked_site(s, Vp);
+        double a[4], b[4];
+        ld4d_nc(base + (size_t)s * 8, a);
+        ld4d_nc(base + (size_t)s * 8 + 4, b);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            v[k] = a[k];
+            v[4 + k] = b[k];
+        }
+        v[8] = __ldg(base + (size_t)8 * Vp + s);
+    }
+};
+
 // ---------------------------------------------------------------------------------------------
 // host-side launchers (one translation unit each)
 // ---------------------------------------------------------------------------------------------

@@ -55,10 +55,11 @@ k_clover_sum(const __grid_constant__ BatchT<CAP> B, const T* __restrict__ clov, 
             T a0[9];
 #pragma unroll
             for (int p = 0; p < 6; ++p) {
-                T a[9];
+                T a[9], a1[9];
+                AhStore<T>::load(cb + (size_t)(p * 2) * 9 * Vp, (int)Vp, s, a);
+                AhStore<T>::load(cb + (size_t)(p * 2 + 1) * 9 * Vp, (int)Vp, s, a1);
 #pragma unroll
-                for (int k = 0; k < 9; ++k)
-                    a[k] = __ldg(cb + (size_t)((p * 2) * 9 + k) * Vp + s) + __ldg(cb + (size_t)((p * 2 + 1) * 9 + k) * Vp + s);
+                for (int k = 0; k < 9; ++k) a[k] += a1[k];
                 if (traceless) {
                     const T tr = (a[0] + a[1] + a[2]) * (T(1) / T(3));
                     a[0] -= tr; a[1] -= tr; a[2] -= tr;
@@ -175,10 +176,11 @@ k_slice_charge(const __grid_constant__ BatchT<CAP> B, const T* __restrict__ clov
             T a0[9], tq = T(0);
 #pragma unroll
             for (int p = 0; p < 6; ++p) {
-                T a[9];
+                T a[9], a1[9];
+                AhStore<T>::load(cb + (size_t)(p * 2) * 9 * Vp, (int)Vp, s, a);
+                AhStore<T>::load(cb + (size_t)(p * 2 + 1) * 9 * Vp, (int)Vp, s, a1);
 #pragma unroll
-                for (int k = 0; k < 9; ++k)
-                    a[k] = __ldg(cb + (size_t)((p * 2) * 9 + k) * Vp + s) + __ldg(cb + (size_t)((p * 2 + 1) * 9 + k) * Vp + s);
+                for (int k = 0; k < 9; ++k) a[k] += a1[k];
                 if (traceless) {
                     const T tr = (a[0] + a[1] + a[2]) * (T(1) / T(3));
                     a[0] -= tr; a[1] -= tr; a[2] -= tr;

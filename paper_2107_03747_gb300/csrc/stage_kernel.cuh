@@ -131,19 +131,13 @@ static __constant__ int8_t c_pair[6][2] = {{0, 1}, {2, 3}, {0, 2}, {1, 3}, {0, 3
 static __constant__ int8_t c_clover_owner[4][4] = {{0, 1, 1, 0}, {0, 0, 1, 1}, {0, 0, 0, 1}, {1, 0, 0, 0}};
 
 // The anti-Hermitian part D - D^+ of a 3x3 matrix as 9 reals (2 Im D_jj; D_jk - conj(D_kj), j<k),
-// written to 9 component planes of length Vp.
+// written to one slot of the clover scratch (AhStore).
 template <class T>
 __device__ __forceinline__ void store_ah(T* __restrict__ p, int Vp, int s, const mat3<T>& d) {
-    s = checked_site(s, Vp);
-    p[0 * (size_t)Vp + s] = T(2) * d.e[0][0].im;
-    p[1 * (size_t)Vp + s] = T(2) * d.e[1][1].im;
-    p[2 * (size_t)Vp + s] = T(2) * d.e[2][2].im;
-    p[3 * (size_t)Vp + s] = d.e[0][1].re - d.e[1][0].re;
-    p[4 * (size_t)Vp + s] = d.e[0][1].im + d.e[1][0].im;
-    p[5 * (size_t)Vp + s] = d.e[0][2].re - d.e[2][0].re;
-    p[6 * (size_t)Vp + s] = d.e[0][2].im + d.e[2][0].im;
-    p[7 * (size_t)Vp + s] = d.e[1][2].re - d.e[2][1].re;
-    p[8 * (size_t)Vp + s] = d.e[1][2].im + d.e[2][1].im;
+    const T v[9] = {T(2) * d.e[0][0].im,           T(2) * d.e[1][1].im,           T(2) * d.e[2][2].im,
+                    d.e[0][1].re - d.e[1][0].re, d.e[0][1].im + d.e[1][0].im, d.e[0][2].re - d.e[2][0].re,
+                    d.e[0][2].im + d.e[2][0].im, d.e[1][2].re - d.e[2][1].re, d.e[1][2].im + d.e[2][1].im};
+    AhStore<T>::store(p, Vp, s, v);
 }
 
 // MODE 0: the RK3 stage.  MODE 1: the stage, and from the same staples of the input field the
