@@ -5,8 +5,9 @@
 // outlook (Sec. 5) is larger N.  This file is the generic-N form of the flow: the same
 // definitions as the SU(3) kernels (twisted staples, Z = -P_ta(U Sigma) with the 1/N trace,
 // Luscher's low-storage RK3, W' = exp(X) W, the clover G = -(i/8)(C - C^+), E, q and the twisted
-// plaquette), written for N x N matrices in registers.  The exponential is summed as its Taylor
-// series after scaling by 2^-s to ||X||_F <= 1/2, then squared s times (SU(2): closed form).
+// plaquette), written for N x N matrices in registers.  The exponential is a Taylor polynomial of
+// degree 7-11 after scaling by 2^-s, evaluated with few products, then squared s times (SU(2):
+// closed form).
 //
 // Storage per configuration and direction: N^2 double2 planes (matrix entries, row-major) of
 // Vp sites; the RK3 accumulator X holds N^2 reals per link: the imaginary parts of the N
@@ -135,9 +136,21 @@ __device__ __forceinline__ void centreN(int k, double& zr, double& zi) {
     sincospi(2.0 * k / N, &zi, &zr);
 }
 
-// exp(X) for anti-Hermitian X: Taylor series of X 2^-s, ||X 2^-s||_F <= 1/2, squared s times
+// exp(X) for anti-Hermitian X: X is scaled by 2^-s to ||Y||_F <= 1/5 and exp(Y) is replaced by
+// its Taylor polynomial T_d of degree d, evaluated by Paterson and Stockmeyer's scheme (SIAM J.
+// Comput. 2 (1973) 60) in blocks of B terms: with M = Y^B, T_d(Y) = B_0 + M (B_1 + M (B_2 + ...)),
+// B_j = sum_{i<B} Y^i / (Bj+i)!, d = B NB - 1 for NB blocks.  B = 3 (Y^2, Y^3, then NB - 1 Horner
+// products) for N <= 3; B = 2 (Y^2, then NB - 1 Horner products) for N = 4, which keeps one
+// matrix fewer live.  The dropped tail is at most ||Y||^{d+1}/(d+1)! e^{||Y||}, so NB follows the
+// norm: the smallest degree whose bound stays under 1.1e-17 (far below FP64 rounding of the
+// unitary result):
+//   B = 3:  d = 8 for ||Y|| <= 0.05,  d = 11 up to 0.2;
+//   B = 2:  d = 7 for ||Y|| <= 0.028, d = 9 for <= 0.088, d = 11 up to 0.2.
+// A flow step of eps = 0.01 has ||X||_F of a few 0.01, so it takes 4 matrix products where the
+// plain series takes one per term (7-9); the result is then squared s times.
 template <int N>
 __device__ void expN(matN<N>& out, const matN<N>& X) {
+    constexpr int B = N >= 4 ? 2 : 3;
     double n2 = 0.0;
 #pragma unroll
     for (int i = 0; i < N; ++i)
@@ -145,39 +158,63 @@ __device__ void expN(matN<N>& out, const matN<N>& X) {
         for (int j = 0; j < N; ++j) n2 += X.e[i][j].re * X.e[i][j].re + X.e[i][j].im * X.e[i][j].im;
     int s = 0;
     double sc = 1.0;
-    while (n2 * sc * sc > 0.25 && s < 60) {
+    while (n2 * sc * sc > 0.04 && s < 60) {
         sc *= 0.5;
         ++s;
     }
-    matN<N> Y, term, t2;
+    n2 *= sc * sc;
+    // blocks and 1/d!
+    int NB;
+    double ctop;
+    if (B == 3) {
+        if (n2 <= 0.05 * 0.05) { NB = 3; ctop = 1.0 / 40320.0; }
+        else { NB = 4; ctop = 1.0 / 39916800.0; }
+    } else {
+        if (n2 <= 0.028 * 0.028) { NB = 4; ctop = 1.0 / 5040.0; }
+        else if (n2 <= 0.088 * 0.088) { NB = 5; ctop = 1.0 / 362880.0; }
+        else { NB = 6; ctop = 1.0 / 39916800.0; }
+    }
+    matN<N> Y, Y2, Y3, t;
 #pragma unroll
     for (int i = 0; i < N; ++i)
 #pragma unroll
-        for (int j = 0; j < N; ++j) {
-            Y.e[i][j] = {X.e[i][j].re * sc, X.e[i][j].im * sc};
-            out.e[i][j] = {i == j ? 1.0 : 0.0, 0.0};
-            term.e[i][j] = out.e[i][j];
+        for (int j = 0; j < N; ++j) Y.e[i][j] = {X.e[i][j].re * sc, X.e[i][j].im * sc};
+    nnN<N, false>(Y2, Y, Y);
+    if constexpr (B == 3) nnN<N, false>(Y3, Y2, Y);
+    const matN<N>& M = B == 3 ? Y3 : Y2;
+    // out = B_j, given ctop = 1/(Bj+B-1)!; returns 1/(Bj)!
+    auto block = [&](int jb, double ct) {
+        double c0 = ct * double(B * jb + B - 1), c1 = ct, c2 = 0.0;
+        if constexpr (B == 3) {
+            c2 = ct;
+            c1 = c0;
+            c0 = c1 * double(B * jb + 1);
         }
-#pragma unroll 1
-    for (int k = 1; k <= 30; ++k) {
-        nnN<N, false>(t2, term, Y);
-        const double inv = 1.0 / k;
-        double mx = 0.0;
 #pragma unroll
         for (int i = 0; i < N; ++i)
 #pragma unroll
             for (int j = 0; j < N; ++j) {
-                term.e[i][j] = {t2.e[i][j].re * inv, t2.e[i][j].im * inv};
-                out.e[i][j].re += term.e[i][j].re;
-                out.e[i][j].im += term.e[i][j].im;
-                mx = fmax(mx, fabs(term.e[i][j].re) + fabs(term.e[i][j].im));
+                cx<double> v = {c1 * Y.e[i][j].re + (i == j ? c0 : 0.0), c1 * Y.e[i][j].im};
+                if constexpr (B == 3) {
+                    v.re += c2 * Y2.e[i][j].re;
+                    v.im += c2 * Y2.e[i][j].im;
+                }
+                out.e[i][j] = v;
             }
-        if (mx < 1e-18) break;
+        return c0;
+    };
+    // top block, then 1/(Bj-1)! = Bj / (Bj)! going down
+    ctop = block(NB - 1, ctop) * double(B * (NB - 1));
+#pragma unroll 1
+    for (int jb = NB - 2; jb >= 0; --jb) {
+        nnN<N, false>(t, M, out);  // M (B_{j+1} + M (...))
+        ctop = block(jb, ctop) * double(B * jb);
+        addN(out, t);
     }
 #pragma unroll 1
     for (int k = 0; k < s; ++k) {
-        t2 = out;
-        nnN<N, false>(out, t2, t2);
+        t = out;
+        nnN<N, false>(out, t, t);
     }
 }
 

@@ -53,6 +53,20 @@ def test_sun_rk3_step_matches_oracle(tgf, N):
         close(got[i], O.measure(ref, TW))
 
 
+@pytest.mark.parametrize("N", [3, 4])
+@pytest.mark.parametrize("eps", [0.2, 0.6])
+def test_sun_large_steps_match_oracle(tgf, N, eps):
+    # RK3 steps whose exponents exceed ||X||_F = 1/8, so the exponential scales by 2^-s and
+    # squares back s >= 1 times; the oracle takes scipy's expm
+    Ls, fs = fields_for(N)
+    b = tgf.SunBatch(N, Ls, any_extents=True)
+    b.set_links(fs)
+    b.step(eps)
+    for f, g in zip(fs, b.get_links()):
+        ref = O.rk3_step(f, eps, TW)
+        assert np.abs(g - ref).max() <= 1e-12
+
+
 def test_sun3_agrees_with_the_su3_kernels(tgf):
     L = (4, 4, 12, 12)
     f = I.random_links(L, 8, 0.5)
