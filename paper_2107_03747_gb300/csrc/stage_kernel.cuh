@@ -322,7 +322,7 @@ k_stage(const __grid_constant__ BatchT<CAP> B, const typename Store<P>::T* __res
                 for (int i = 0; i < 3; ++i)
 #pragma unroll
                     for (int j = 0; j < 3; ++j)
-                        rt += a.e[i][j].re * f.e[j][i].re - a.e[i][j].im * f.e[j][i].im;
+                        rt = fma(a.e[i][j].re, f.e[j][i].re, fma(-a.e[i][j].im, f.e[j][i].im, rt));
                 cb[(size_t)(108 + pl) * Vp + s] = T(3) - rt;
                 // K = F - B; D1 = U K (site n), D2 = K U (site n + mu).  A plane built through its
                 // second direction (nu < mu) takes K = B - F: the leaves of the plane (mu, nu) are the

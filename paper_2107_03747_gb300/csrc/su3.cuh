@@ -38,6 +38,13 @@ __device__ __forceinline__ void add_to(mat3<T>& a, const mat3<T>& b) {
         }
 }
 
+// Products rounded on their own, never contracted into a neighbouring add.  The scalar sums below
+// that mix products and adds are written as explicit chains of fma and mul_rn, so every kernel
+// that inlines them rounds the same way (the compiler may otherwise contract a b - c d either way,
+// and differently in different kernels).
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+
 // a *= (zr + i zi)
 template <class T>
 __device__ __forceinline__ void scale_cx(mat3<T>& a, T zr, T zi) {
@@ -45,9 +52,9 @@ __device__ __forceinline__ void scale_cx(mat3<T>& a, T zr, T zi) {
     for (int i = 0; i < 3; ++i)
 #pragma unroll
         for (int j = 0; j < 3; ++j) {
-            T r = a.e[i][j].re, m = a.e[i][j].im;
-            a.e[i][j].re = r * zr - m * zi;
-            a.e[i][j].im = r * zi + m * zr;
+            const T r = a.e[i][j].re, m = a.e[i][j].im;
+            a.e[i][j].re = fma(r, zr, -mul_rn(m, zi));
+            a.e[i][j].im = fma(r, zi, mul_rn(m, zr));
         }
 }
 
@@ -457,11 +464,12 @@ __device__ __forceinline__ void rebuild_row2(mat3<T>& u) {
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
         const int a = (j + 1) % 3, b = (j + 2) % 3;
-        // (r0_a r1_b - r0_b r1_a)^*
-        T re = u.e[0][a].re * u.e[1][b].re - u.e[0][a].im * u.e[1][b].im
-             - (u.e[0][b].re * u.e[1][a].re - u.e[0][b].im * u.e[1][a].im);
-        T im = u.e[0][a].re * u.e[1][b].im + u.e[0][a].im * u.e[1][b].re
-             - (u.e[0][b].re * u.e[1][a].im + u.e[0][b].im * u.e[1][a].re);
+        // (p q - r v)^* with p = r0_a, q = r1_b, r = r0_b, v = r1_a
+        const cx<T> p = u.e[0][a], q = u.e[1][b], r = u.e[0][b], v = u.e[1][a];
+        const T rv_re = fma(r.re, v.re, -mul_rn(r.im, v.im));
+        const T rv_im = fma(r.re, v.im, mul_rn(r.im, v.re));
+        const T re = fma(p.re, q.re, fma(-p.im, q.im, -rv_re));
+        const T im = fma(p.re, q.im, fma(p.im, q.re, -rv_im));
         u.e[2][j] = {re, -im};
     }
 }
