@@ -182,8 +182,8 @@ __device__ void expN(matN<N>& out, const matN<N>& X) {
     nnN<N, false>(Y2, Y, Y);
     if constexpr (B == 3) nnN<N, false>(Y3, Y2, Y);
     const matN<N>& M = B == 3 ? Y3 : Y2;
-    // out = B_j, given ctop = 1/(Bj+B-1)!; returns 1/(Bj)!
-    auto block = [&](int jb, double ct) {
+    // dst = B_j, given ctop = 1/(Bj+B-1)!; returns 1/(Bj)!
+    auto block = [&](matN<N>& dst, int jb, double ct) {
         double c0 = ct * double(B * jb + B - 1), c1 = ct, c2 = 0.0;
         if constexpr (B == 3) {
             c2 = ct;
@@ -199,17 +199,18 @@ __device__ void expN(matN<N>& out, const matN<N>& X) {
                     v.re += c2 * Y2.e[i][j].re;
                     v.im += c2 * Y2.e[i][j].im;
                 }
-                out.e[i][j] = v;
+                dst.e[i][j] = v;
             }
         return c0;
     };
-    // top block, then 1/(Bj-1)! = Bj / (Bj)! going down
-    ctop = block(NB - 1, ctop) * double(B * (NB - 1));
+    // top block, then 1/(Bj-1)! = Bj / (Bj)! going down; each Horner step forms B_j first and
+    // accumulates the product M (B_{j+1} + ...) onto it in the product's own FMAs
+    ctop = block(out, NB - 1, ctop) * double(B * (NB - 1));
 #pragma unroll 1
     for (int jb = NB - 2; jb >= 0; --jb) {
-        nnN<N, false>(t, M, out);  // M (B_{j+1} + M (...))
-        ctop = block(jb, ctop) * double(B * jb);
-        addN(out, t);
+        ctop = block(t, jb, ctop) * double(B * jb);
+        nnN<N, true>(t, M, out);
+        out = t;
     }
 #pragma unroll 1
     for (int k = 0; k < s; ++k) {
