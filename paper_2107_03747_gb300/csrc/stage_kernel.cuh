@@ -102,13 +102,14 @@ __device__ __forceinline__ bool cube_site(const CfgDesc& c, int b, int lane, int
 // direction warps of a plane one forms T and the other reads it from shared memory.  The
 // producer signals with bar.arrive on the plane's named barrier (64 threads: both warps) and goes
 // on; the consumer waits with bar.sync.  Order of nu per warp mu and which planes it forms: every
-// warp forms its planes before it reads any, and no plane is read before its producer's first
-// product, so no wait can close a cycle:
-//   mu 0: nu 1 (forms 01), 2 (reads 02), 3 (reads 03)
+// warp forms its planes before it reads any, so no wait can close a cycle, and every plane is
+// read at a later position of the reader's order than the one at which its producer forms it,
+// so a consumer rarely finds its corner not yet written:
+//   mu 0: nu 1 (forms 01), 3 (reads 03), 2 (reads 02)
 //   mu 1: nu 2 (forms 12), 3 (forms 13), 0 (reads 01)
-//   mu 2: nu 0 (forms 02), 3 (forms 23), 1 (reads 12)
-//   mu 3: nu 0 (forms 03), 1 (reads 13), 2 (reads 23)
-static __constant__ int8_t c_pair_nu[4][3] = {{1, 2, 3}, {2, 3, 0}, {0, 3, 1}, {0, 1, 2}};
+//   mu 2: nu 3 (forms 23), 0 (forms 02), 1 (reads 12)
+//   mu 3: nu 0 (forms 03), 2 (reads 23), 1 (reads 13)
+static __constant__ int8_t c_pair_nu[4][3] = {{1, 3, 2}, {2, 3, 0}, {3, 0, 1}, {0, 2, 1}};
 static __constant__ int8_t c_pair_own[4][4] = {{0, 1, 0, 0}, {0, 0, 1, 1}, {1, 0, 0, 1}, {1, 0, 0, 0}};
 __device__ __forceinline__ void bar_arrive(int id, int nthreads) {
     asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
