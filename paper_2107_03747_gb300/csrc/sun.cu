@@ -7,7 +7,7 @@
 // Luscher's low-storage RK3, W' = exp(X) W, the clover G = -(i/8)(C - C^+), E, q and the twisted
 // plaquette), written for N x N matrices in registers.  The exponential is a Taylor polynomial of
 // degree 7-11 after scaling by 2^-s, evaluated with few products, then squared s times (SU(2):
-// closed form).
+// closed form; SU(3): the Cayley-Hamilton form of the SU(3) kernels).
 //
 // Storage per configuration and direction: N^2 double2 planes (matrix entries, row-major) of
 // Vp sites; the RK3 accumulator X holds N^2 reals per link: the imaginary parts of the N
@@ -16,6 +16,7 @@
 #include <math_constants.h>
 #include <stdint.h>
 
+#include "expm.cuh"
 #include "lattice.cuh"
 
 namespace tgf {
@@ -238,6 +239,28 @@ __device__ void expN<2>(matN<2>& out, const matN<2>& X) {
     out.e[0][1] = {er * m01.re - ei * m01.im, er * m01.im + ei * m01.re};
     out.e[1][0] = {er * m10.re - ei * m10.im, er * m10.im + ei * m10.re};
     out.e[1][1] = {er * m11.re - ei * m11.im, er * m11.im + ei * m11.re};
+}
+
+// SU(3): the Cayley-Hamilton exponential of the SU(3) kernels (expm.cuh) on the 8 parameters of
+// the traceless X (the stage builds X traceless; a trace at rounding level is dropped): a few
+// dozen scalar operations instead of the polynomial's 4 matrix products.
+template <>
+__device__ void expN<3>(matN<3>& out, const matN<3>& X) {
+    alg8<double> x;
+    x.v[0] = X.e[0][0].im;
+    x.v[1] = X.e[1][1].im;
+    x.v[2] = X.e[0][1].re;
+    x.v[3] = X.e[0][1].im;
+    x.v[4] = X.e[0][2].re;
+    x.v[5] = X.e[0][2].im;
+    x.v[6] = X.e[1][2].re;
+    x.v[7] = X.e[1][2].im;
+    mat3<double> m;
+    expm_su3<double, false>(m, x);
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) out.e[i][j] = m.e[i][j];
 }
 
 // one RK3 stage for SU(N); block = 4 warps (one per direction) x 32 sites
