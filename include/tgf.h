@@ -278,9 +278,10 @@ tgf_status tgf_ctx_load(tgf_ctx *ctx, const char *path, double *t, long long *st
 /* The paper defines the coupling for SU(N) on the l x l x (Nl) x (Nl) box with the twist
  * exp(2 pi i k / N) and gives numbers for N = 3; these calls run the same flow and measurement
  * for N = 2, 3, 4 in FP64: Z = -P_ta(U Sigma) with the 1/N trace, Luscher's RK3 as in tgf_stage,
- * exp(X) by a Taylor polynomial of degree 7 to 11 (chosen by ||X||_F, tail under 1.1e-17) after
- * scaling X by 2^-s to ||X||_F <= 1/5, evaluated by Paterson and Stockmeyer's scheme, and squaring back
- * (N = 2: the closed form e^{i tau}(cos theta + sin theta / theta X0)), the
+ * exp(X) for N = 4 by a Taylor polynomial of degree 7 to 11 (chosen by ||X||_F, tail under
+ * 1.1e-17) after scaling X by 2^-s to ||X||_F <= 1/5, evaluated by Paterson and Stockmeyer's
+ * scheme, and squaring back (N = 2: the closed form e^{i tau}(cos theta + sin theta / theta X0);
+ * N = 3: the Cayley-Hamilton form of tgf_stage), the
  * twisted clover and plaquette as in tgf_measure with the twist n_{mu nu} taken mod N and
  * P = (1/(6V)) sum_n sum_{mu<nu} (1/N) Re Tr[Z* P_{mu nu}].  Canonical buffers hold V x 4 x N x N
  * complex doubles per configuration ([x3][x2][x1][x0][mu][row][col][re,im]); device storage is
